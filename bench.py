@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 enumeration path.
+
+A step = one pass of the hot path over the resident workload: gpm_count of
+every pattern of the workload on the device-resident, already-oriented graph
+(preprocessing excluded, as in the paper's evaluation, Section 8).  Default
+workload: 4-clique and 5-clique counting on the seeded R-MAT scale-22 graph
+(4.19M vertices, edge factor 16, (0.57, 0.19, 0.19, 0.05)).
+
+Prints ONE JSON line (rank 0).  `value` = undirected edges of G processed per
+second per step (both patterns), summed over ranks; `e2e` repeats the step
+through the public C ABI from pinned host arrays (load + orient + plan + count,
+host->device copies inside the timed region); `roofline` compares the
+dominant kernel's algorithmic bytes per second with the measured HBM copy
+peak; `cpu_baseline` is the CPU oracle on a bounded random sample of the same
+root tasks, all host cores.  `--impl reference` times that oracle alone.
+
+Multi-GPU (torchrun): every rank runs its own replica of the workload (weak
+scaling); ranks only meet in barriers and the max-time reduction.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "rmat22": {"patterns": ["4-clique", "5-clique"], "induced": False,
+               "desc": "R-MAT scale 22, edge factor 16, (0.57,0.19,0.19,0.05), seed 2"},
+    "er-10k": {"patterns": ["triangle"], "induced": False,
+               "desc": "Erdos-Renyi G(n=10000, m=80000), seed 1"},
+    "chunglu-1m": {"patterns": ["diamond", "4-cycle"], "induced": False,
+                   "desc": "Chung-Lu n=1e6, 32M endpoint pairs, gamma 2.1, seed 3"},
+}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_sample(g, patterns, induced, target_s: float, nthreads: int, seed: int = 7):
+    """Time the oracle on random contiguous task ranges; returns per-pattern
+    (sampled tasks, total tasks, seconds) scaled up to the whole workload."""
+    import oracle as O
+    out = {}
+    rng = np.random.default_rng(seed)
+    per_pat = target_s / len(patterns)
+    for pat in patterns:
+        nt = O.num_tasks(g, pat)
+        span, nranges, sampled, secs = 64, 16, 0, 0.0
+        while True:
+            starts = rng.integers(0, max(1, nt - span), nranges)
+            ranges = [(int(s), int(min(nt, s + span))) for s in starts]
+            _, t = O.count_ranges(g, pat, ranges, induced, nthreads=nthreads)
+            sampled += sum(b - a for a, b in ranges)
+            secs += t
+            if secs >= per_pat or sampled >= nt:
+                break
+            nranges = min(4096, nranges * 2)
+        out[pat] = (sampled, nt, secs)
+    return out
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle as it stands, on the machine's host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import graphgen as gg
+    wl = WORKLOADS[args.workload]
+    g = gg.workload(args.workload)
+    nthreads = os.cpu_count() or 1
+    times = []
+    for i in range(args.warmup + args.steps):
+        samp = cpu_sample(g, wl["patterns"], wl["induced"], args.cpu_seconds / 2, nthreads, seed=100 + i)
+        est = sum(secs * nt / max(1, s) for (s, nt, secs) in samp.values())
+        if i >= args.warmup:
+            times.append(est)
+    t = statistics.mean(times)
+    val = g.m / t
+    line = {"impl": "reference", "metric": "edges/s", "value": val, "unit": "edges/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": args.workload, "graph": wl["desc"], "patterns": wl["patterns"],
+                       "n": g.n, "edges": g.m},
+            "cpu_baseline": {"value": val, "unit": "edges/s", "cores": nthreads, "kind": "oracle",
+                             "sample": "random contiguous root-task ranges, count scaled by "
+                                       "total/sampled tasks per pattern"},
+            "e2e": {"value": val, "unit": "edges/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import graphgen as gg
+    import paper_2112_09761_gb300 as G
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    G.build()
+    wl = WORKLOADS[args.workload]
+    pats, induced = wl["patterns"], wl["induced"]
+    t0 = time.time()
+    g = gg.workload(args.workload)
+    gen_s = time.time() - t0
+    stream = torch.cuda.current_stream()
+
+    # ---- preprocessing (excluded from the step): load, validate, orient, plan
+    tp = time.time()
+    graph = G.Graph.from_csr(g)
+    plans = {p: graph.plan(p, induced) for p in pats}
+    torch.cuda.synchronize()
+    prep_s = time.time() - tp
+    counts = {p: G.gpm_count(plans[p]) for p in pats}
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        for p in pats:
+            G.gpm_count(plans[p])
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    ev = {p: [] for p in pats}
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(args.steps):
+        for p in pats:
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            c = G.gpm_count(plans[p])
+            b.record(stream)
+            ev[p].append((a, b))
+            assert c == counts[p], f"count changed between runs: {p}"
+    stop.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    total_ms = start.elapsed_time(stop)
+    per_pat_s = {p: statistics.mean(a.elapsed_time(b) for a, b in ev[p]) / 1e3 for p in pats}
+    step_s = total_ms / 1e3 / args.steps
+    if dist is not None:
+        t = torch.tensor([step_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_s = float(t.item())
+    value = world * g.m / step_s
+
+    # ---- algorithmic bytes of the dominant kernel (separate, untimed stats run)
+    dom = max(pats, key=lambda p: per_pat_s[p])
+    sp = G.gpm_plan(graph.handle, dom, induced, G.GPM_COUNT, {"collect_stats": 1})
+    assert G.gpm_count(sp) == counts[dom]
+    st = G.gpm_plan_stats(sp)
+    G.gpm_plan_free(sp)
+    hbm, peak_kind = peaks()
+    achieved = st["alg_bytes"] / per_pat_s[dom] / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "kernel": f"k_clique<{dom}>"
+                if "clique" in dom or dom == "triangle" else f"k_enum<{dom}>",
+                "alg_bytes_per_launch": st["alg_bytes"], "set_ops_per_launch": st["set_ops"],
+                "peak_kind": peak_kind}
+
+    # ---- end to end through the public API from pinned host memory
+    off_h = torch.from_numpy(g.offsets).pin_memory()
+    nbr_h = torch.from_numpy(g.nbrs.view(np.int32)).pin_memory()
+    e2e_times = []
+    for i in range(args.e2e_steps + 1):
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h = G.gpm_load_csr(off_h.numpy(), nbr_h.numpy().view(np.uint32), g.n)
+        for p in pats:
+            pl = G.gpm_plan(h, p, induced)
+            c = G.gpm_count(pl)
+            assert c == counts[p]
+            G.gpm_plan_free(pl)
+        G.gpm_graph_free(h)
+        b.record(stream)
+        barrier()
+        if i > 0:  # first pass warms the allocator
+            e2e_times.append(a.elapsed_time(b) / 1e3)
+    e2e_s = statistics.mean(e2e_times) if e2e_times else float("nan")
+    h2d = g.offsets.nbytes + g.nbrs.nbytes
+    d2h = len(pats) * 8
+
+    # ---- CPU oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        nthreads = os.cpu_count() or 1
+        samp = cpu_sample(g, pats, induced, args.cpu_seconds, nthreads)
+        est = sum(secs * nt / max(1, s) for (s, nt, secs) in samp.values())
+        cpu = {"value": g.m / est, "unit": "edges/s", "cores": nthreads, "kind": "oracle",
+               "sample": "; ".join(f"{p}: {s} of {nt} root tasks in random 64-task ranges, "
+                                   f"{secs:.1f} s" for p, (s, nt, secs) in samp.items()),
+               "est_full_s": est}
+
+    if rank == 0:
+        line = {
+            "metric": "edges/s", "value": value, "unit": "edges/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "graph": wl["desc"], "patterns": pats,
+                       "induced": induced, "n": g.n, "edges": g.m,
+                       "max_degree": graph.info()["max_degree"],
+                       "max_out_degree": graph.info()["max_out_degree"],
+                       "l2": "inputs larger than L2 (CSR + DAG > 129 MB)",
+                       "parallelism": f"replicas x{world}"},
+            "per_pattern_s": per_pat_s, "counts": counts,
+            "prep_s": prep_s, "gen_s": gen_s,
+            "gpu_launches": len(pats) * args.steps,
+            "clocks": clocks,
+            "roofline": roofline,
+            "e2e": {"value": world * g.m / e2e_s, "unit": "edges/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "s_per_step": e2e_s},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    graph.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/*
+ * gpm.h — C ABI of the GB300 pattern-aware subgraph enumeration library.
+ *
+ * The library counts and lists the matches of a small pattern P in a large
+ * undirected data graph G (G2Miner, arXiv 2112.09761).  A match is one
+ * distinct subgraph of G isomorphic to P, found once (completeness and
+ * uniqueness, Section 2.1; symmetry order, Section 2.2).  Vertex-induced
+ * matches require P's non-edges to be non-edges of G; edge-induced matches do
+ * not (Section 2.1).  For cliques the two coincide.
+ *
+ * Everything on the enumeration path runs in this library's own CUDA kernels
+ * for sm_103a: loading and validating the CSR, orienting it, building the root
+ * task list, the warp-cooperative DFS with set intersection / difference /
+ * bounding, the reductions and the listing output.  There is no CPU fallback:
+ * a process without a usable GPU gets GPM_E_CUDA.
+ *
+ * Conventions
+ *   - Every call returns a gpm_status.  On error nothing is written to the
+ *     outputs and gpm_last_error() (thread-local) describes the failure.
+ *   - Handles (gpm_graph, gpm_plan_t) are opaque and library-owned.
+ *   - `stream` arguments are cudaStream_t values passed as void*; NULL is the
+ *     legacy default stream.  Calls that return host results synchronise that
+ *     stream before returning.
+ *   - Vertex IDs are uint32; counts are uint64; all arithmetic is integer.
+ *   - A handle may be used by one host thread at a time.
+ */
+#ifndef GPM_H_
+#define GPM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gpm_status {
+  GPM_OK = 0,
+  GPM_E_INVALID_ARG = 1,         /* NULL pointer, bad size, bad flag combination */
+  GPM_E_UNSORTED = 2,            /* a neighbour list is not strictly ascending */
+  GPM_E_SELF_LOOP = 3,           /* v appears in N(v) */
+  GPM_E_DUPLICATE = 4,           /* a neighbour appears twice in one list */
+  GPM_E_ASYMMETRIC = 5,          /* u in N(v) but v not in N(u) */
+  GPM_E_OOM = 6,                 /* a device or pinned-host allocation failed */
+  GPM_E_UNSUPPORTED_PATTERN = 7, /* the pattern matches no plan family */
+  GPM_E_CAPACITY = 8,            /* listing output truncated (n_total still valid) */
+  GPM_E_TIMEOUT = 9,             /* a bounded device-side wait gave up */
+  GPM_E_CUDA = 10,               /* CUDA runtime error (no device, launch failure, ...) */
+  GPM_E_RANGE = 11               /* an ID or offset outside [0, n) / [0, nnz] */
+} gpm_status;
+
+/* ------------------------------------------------------------ patterns */
+
+/* A pattern: k <= 8 vertices (0..k-1) and an undirected edge list.  The
+ * pattern must be connected.  (Section 4.1: patterns are given explicitly by
+ * their edge list, or by helpers such as generateClique.) */
+typedef struct gpm_pattern {
+  uint32_t k;
+  uint32_t n_edges;
+  uint8_t edges[28][2];
+} gpm_pattern;
+
+/* Fill *out with a named pattern.  Names: "triangle", "<k>-clique" (k=3..8),
+ * "diamond", "4-cycle", "tailed-triangle", "3-star", "4-path", "wedge".
+ * The edge list is given in the library's matching order, i.e. the order in
+ * which gpm_list() writes the k vertices of each match:
+ *   k-clique         v1..vk in the degree-orientation order of the clique
+ *   diamond          (v1,v2) the chord, v3 > v4 the other two
+ *   4-cycle          v1 = the largest ID, cycle v1-v2-v3-v4-v1, v2 > v4
+ *   tailed-triangle  v1 the degree-3 vertex, triangle v1 v2 v3 (v3 < v2), tail v4
+ *   3-star           centre v1, leaves v2 > v3 > v4
+ *   4-path           path v3-v1-v2-v4, middle edge v1 > v2
+ *   wedge            centre v1, ends v2 > v3
+ * Returns GPM_E_UNSUPPORTED_PATTERN for an unknown name. */
+gpm_status gpm_pattern_named(const char* name, gpm_pattern* out);
+
+/* -------------------------------------------------------------- graphs */
+
+typedef struct gpm_graph gpm_graph;
+
+#define GPM_DEVICE_PTRS 1u   /* offsets / nbrs are device pointers (else host) */
+#define GPM_BORROW 2u        /* keep the caller's device arrays instead of copying;
+                                needs GPM_DEVICE_PTRS and 64-bit offsets; the caller
+                                keeps them alive and unchanged until gpm_graph_free */
+#define GPM_SKIP_VALIDATE 4u /* trust the input (no sortedness / symmetry check) */
+
+/*
+ * Load an undirected data graph in CSR form (Section 4.2 graph loader).
+ *   offsets      n+1 row offsets, int32 (offsets_is_64 = 0) or int64 (= 1);
+ *                offsets[0] = 0, non-decreasing, offsets[n] = nnz
+ *   nbrs         nnz uint32 neighbour IDs; row v is nbrs[offsets[v] ..
+ *                offsets[v+1]); each row strictly ascending, no v in N(v),
+ *                and u in N(v) iff v in N(u) (both directions present)
+ *   n, nnz       vertices and directed entries (nnz = 2|E|); n < 2^32 - 1
+ *   flags        GPM_DEVICE_PTRS | GPM_BORROW | GPM_SKIP_VALIDATE
+ *   stream       stream for the copies and the validation kernels
+ * The library copies the arrays to device memory it owns (int64 offsets),
+ * computes degrees and the maximum degree, and (unless skipped) validates the
+ * input on the GPU, returning GPM_E_UNSORTED / _SELF_LOOP / _DUPLICATE /
+ * _ASYMMETRIC / _RANGE for the first violation class found.
+ * Derived structures (degree-oriented DAG, root task lists) are built on the
+ * device the first time a plan needs them and cached with the graph.
+ */
+gpm_status gpm_load_csr(const void* offsets, int offsets_is_64, const uint32_t* nbrs, uint32_t n,
+                        uint64_t nnz, uint32_t flags, void* stream, gpm_graph** out);
+
+/* Input information extracted while loading (Section 4.2: |V|, |E|, max
+ * degree).  Any output pointer may be NULL.  max_out_degree is the maximum
+ * out-degree of the degree-oriented DAG (0 until a clique plan built it). */
+gpm_status gpm_graph_info(const gpm_graph* g, uint32_t* n, uint64_t* n_edges, uint32_t* max_degree,
+                          uint32_t* max_out_degree);
+
+/* Release the graph and everything cached with it.  NULL is ignored. */
+void gpm_graph_free(gpm_graph* g);
+
+/* --------------------------------------------------------------- plans */
+
+typedef struct gpm_plan_s gpm_plan_t;
+
+#define GPM_COUNT 0
+#define GPM_LIST 1
+
+/* Execution knobs.  Zero means "choose automatically" for every field. */
+typedef struct gpm_plan_opts {
+  uint32_t warps_per_block;  /* warps per CTA of the enumeration kernel */
+  uint32_t blocks_per_sm;    /* resident CTAs per SM of the persistent grid */
+  uint32_t chunk;            /* root tasks taken per grab from the task queue */
+  uint32_t bsearch_ratio;    /* |B| >= ratio * |A| selects binary search over merge */
+  uint32_t no_count_only;    /* 1 = enumerate even where a counting-only form exists */
+  uint32_t collect_stats;    /* 1 = count algorithmic bytes / set operations (slower) */
+  uint32_t no_lgs;           /* 1 = cliques without local graph search (sorted sets only) */
+  uint32_t reserved[1];
+} gpm_plan_opts;
+
+/*
+ * Build an execution plan (Section 4.2 pattern analyzer, Section 7.2 memory
+ * management) for counting or listing `pattern` in `g`:
+ *   induced   0 = edge-induced, 1 = vertex-induced
+ *   mode      GPM_COUNT or GPM_LIST
+ *   opts      NULL for automatic choices
+ * The pattern is identified up to isomorphism with one of the named families
+ * (k-clique up to k = 8, diamond, 4-cycle, tailed-triangle, 3-star, 4-path,
+ * wedge); anything else returns GPM_E_UNSUPPORTED_PATTERN.  The plan fixes the
+ * matching order, the symmetry order, the root task list Omega (reduced to
+ * v1 > v2 when the symmetry order allows, Section 7.2 (2)), the per-warp DFS
+ * buffers (Section 7.2 (3)) and the grid; it builds the DAG / task lists on
+ * the device if the graph has not cached them yet.
+ */
+gpm_status gpm_plan(gpm_graph* g, const gpm_pattern* pattern, int induced, int mode,
+                    const gpm_plan_opts* opts, void* stream, gpm_plan_t** out);
+
+/* Number of root tasks |Omega| of the plan: DAG arcs for cliques (listed by
+ * source then destination ID), pairs v1 > v2 for diamond / 4-cycle / 4-path
+ * (by v1 then v2), and all directed CSR entries for tailed-triangle / 3-star /
+ * wedge (CSR order).  This order defines the task ranges of gpm_count_range. */
+gpm_status gpm_plan_info(const gpm_plan_t* p, uint64_t* n_tasks, uint32_t* k);
+
+/* Count all matches (Section 4.1 count()).  *out_count is a host uint64.
+ * Synchronises `stream`. */
+gpm_status gpm_count(gpm_plan_t* p, uint64_t* out_count, void* stream);
+
+/* Count the matches rooted at tasks [task_lo, task_hi) of Omega (clamped to
+ * |Omega|).  Summing disjoint ranges gives gpm_count's result. */
+gpm_status gpm_count_range(gpm_plan_t* p, uint64_t task_lo, uint64_t task_hi, uint64_t* out_count,
+                           void* stream);
+
+/*
+ * List matches (Section 4.1 list()).  Writes at most `capacity` matches of k
+ * uint32 each (the plan's matching order, see gpm_pattern_named) to the
+ * DEVICE buffer out_dev (capacity * k uint32), in an unspecified order.
+ * *n_written = min(total, capacity), *n_total = all matches.  Returns
+ * GPM_E_CAPACITY (with both outputs valid) when the buffer was too small.
+ * The plan must have been built with GPM_LIST.  Synchronises `stream`.
+ */
+gpm_status gpm_list(gpm_plan_t* p, uint32_t* out_dev, uint64_t capacity, uint64_t* n_written,
+                    uint64_t* n_total, void* stream);
+
+/*
+ * Statistics of the plan's last gpm_count / gpm_count_range / gpm_list call,
+ * available when the plan was built with collect_stats = 1 (GPM_E_INVALID_ARG
+ * otherwise).  alg_bytes sums, over every set operation A∘B of the DFS
+ * (Section 6.1), 4 * (min(|A|,|B|) + min(max(|A|,|B|), min(|A|,|B|) *
+ * ceil(log2(max(|A|,|B|) + 1)))) bytes of operands (the cheaper of a merge
+ * and a binary search), 16 B of list offsets and 4 B per written element, plus
+ * 8 B per root task; set_ops counts the set operations.  Both are integers
+ * independent of the schedule.
+ */
+gpm_status gpm_plan_stats(const gpm_plan_t* p, uint64_t* alg_bytes, uint64_t* set_ops);
+
+/* Release the plan.  NULL is ignored. */
+void gpm_plan_free(gpm_plan_t* p);
+
+/* ------------------------------------------------------------- errors */
+
+/* Description of the last error on this host thread ("" if none). */
+const char* gpm_last_error(void);
+
+/* Library version string. */
+const char* gpm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPM_H_ */

@@ -76,6 +76,10 @@ def _L():
         lib.og_count.restype = ctypes.c_int
         lib.og_count.argtypes = [i64p, u32p, ctypes.c_uint32, ctypes.c_int, ctypes.c_uint32,
                                  ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, u64p]
+        lib.og_count_ranges.restype = ctypes.c_int
+        lib.og_count_ranges.argtypes = [i64p, u32p, ctypes.c_uint32, ctypes.c_int, ctypes.c_uint32,
+                                        ctypes.c_int, u64p, ctypes.c_uint64, ctypes.c_int, u64p,
+                                        ctypes.POINTER(ctypes.c_double)]
         lib.og_list.restype = ctypes.c_int
         lib.og_list.argtypes = [i64p, u32p, ctypes.c_uint32, ctypes.c_int, ctypes.c_uint32,
                                 ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, u32p,
@@ -126,6 +130,23 @@ def count(g, pattern: str, induced: bool = False, task_lo: int = 0, task_hi: int
     _check(_L().og_count(po, pn, g.n, fam, k, int(induced), task_lo, hi, nthreads,
                          ctypes.byref(out)))
     return out.value
+
+
+def count_ranges(g, pattern: str, ranges, induced: bool = False,
+                 nthreads: int = 1) -> tuple[int, float]:
+    """O2 count summed over task ranges [(lo, hi), ...]; returns (count, seconds
+    of the counting phase, setup excluded)."""
+    fam, k, _ = PATTERNS[pattern]
+    off, nbr, po, pn = _arrs(g)
+    rr = np.asarray(ranges, dtype=np.uint64).reshape(-1)
+    if len(rr) == 0:
+        return 0, 0.0
+    out = ctypes.c_uint64(0)
+    sec = ctypes.c_double(0.0)
+    _check(_L().og_count_ranges(po, pn, g.n, fam, k, int(induced),
+                                rr.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), len(rr) // 2,
+                                nthreads, ctypes.byref(out), ctypes.byref(sec)))
+    return out.value, sec.value
 
 
 def list_matches(g, pattern: str, induced: bool = False, task_lo: int = 0,

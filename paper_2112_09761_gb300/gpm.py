@@ -1,0 +1,289 @@
+"""Thin ctypes binding of the C ABI in include/gpm.h (argument marshalling only).
+
+Every function here has the name of the C entry point it wraps and does no
+computation of its own: all enumeration work runs in libgpm.so's CUDA kernels.
+If the library has not been built, or the process has no GPU, calls fail
+loudly (RuntimeError / GpmError with GPM_E_CUDA); there is no CPU fallback.
+
+PyTorch is used only for device memory (listing buffers, device-resident CSR
+arrays) and for the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import _build
+
+GPM_OK = 0
+STATUS = {0: "GPM_OK", 1: "GPM_E_INVALID_ARG", 2: "GPM_E_UNSORTED", 3: "GPM_E_SELF_LOOP",
+          4: "GPM_E_DUPLICATE", 5: "GPM_E_ASYMMETRIC", 6: "GPM_E_OOM",
+          7: "GPM_E_UNSUPPORTED_PATTERN", 8: "GPM_E_CAPACITY", 9: "GPM_E_TIMEOUT",
+          10: "GPM_E_CUDA", 11: "GPM_E_RANGE"}
+GPM_E_CAPACITY = 8
+GPM_DEVICE_PTRS, GPM_BORROW, GPM_SKIP_VALIDATE = 1, 2, 4
+GPM_COUNT, GPM_LIST = 0, 1
+
+
+class GpmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class gpm_pattern(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_uint32), ("n_edges", ctypes.c_uint32),
+                ("edges", (ctypes.c_uint8 * 2) * 28)]
+
+    def edge_list(self):
+        return [(int(self.edges[i][0]), int(self.edges[i][1])) for i in range(self.n_edges)]
+
+
+class gpm_plan_opts(ctypes.Structure):
+    _fields_ = [("warps_per_block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
+                ("chunk", ctypes.c_uint32), ("bsearch_ratio", ctypes.c_uint32),
+                ("no_count_only", ctypes.c_uint32), ("collect_stats", ctypes.c_uint32),
+                ("no_lgs", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 1)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libgpm.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgpm.so is not built ({path}); run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        vp, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        L.gpm_last_error.restype = ctypes.c_char_p
+        L.gpm_version.restype = ctypes.c_char_p
+        L.gpm_pattern_named.argtypes = [ctypes.c_char_p, ctypes.POINTER(gpm_pattern)]
+        L.gpm_load_csr.argtypes = [vp, ctypes.c_int, vp, u32, u64, u32, vp, ctypes.POINTER(vp)]
+        L.gpm_graph_info.argtypes = [vp, u32p, u64p, u32p, u32p]
+        L.gpm_graph_free.argtypes = [vp]
+        L.gpm_graph_free.restype = None
+        L.gpm_plan.argtypes = [vp, ctypes.POINTER(gpm_pattern), ctypes.c_int, ctypes.c_int,
+                               ctypes.POINTER(gpm_plan_opts), vp, ctypes.POINTER(vp)]
+        L.gpm_plan_info.argtypes = [vp, u64p, u32p]
+        L.gpm_count.argtypes = [vp, u64p, vp]
+        L.gpm_count_range.argtypes = [vp, u64, u64, u64p, vp]
+        L.gpm_list.argtypes = [vp, vp, u64, u64p, u64p, vp]
+        L.gpm_plan_stats.argtypes = [vp, u64p, u64p]
+        L.gpm_plan_free.argtypes = [vp]
+        L.gpm_plan_free.restype = None
+        for name in ("gpm_pattern_named", "gpm_load_csr", "gpm_graph_info", "gpm_plan",
+                     "gpm_plan_info", "gpm_count", "gpm_count_range", "gpm_list", "gpm_plan_stats"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/gpm.h."""
+    path = os.path.join(_build.ROOT, "include", "gpm.h")
+    with open(path) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gpm_[a-z_0-9]+)\s*\(", text)))
+
+
+def _check(status: int):
+    if status != GPM_OK:
+        raise GpmError(status, gpm_last_error())
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return ctypes.c_void_p(0)
+
+
+def gpm_last_error() -> str:
+    return lib().gpm_last_error().decode()
+
+
+def gpm_version() -> str:
+    return lib().gpm_version().decode()
+
+
+def gpm_pattern_named(name: str) -> gpm_pattern:
+    p = gpm_pattern()
+    _check(lib().gpm_pattern_named(name.encode(), ctypes.byref(p)))
+    return p
+
+
+def pattern_from_edges(k: int, edges) -> gpm_pattern:
+    p = gpm_pattern()
+    p.k = k
+    edges = list(edges)
+    p.n_edges = len(edges)
+    for i, (a, b) in enumerate(edges):
+        p.edges[i][0] = a
+        p.edges[i][1] = b
+    return p
+
+
+def gpm_load_csr(offsets, nbrs, n: int | None = None, flags: int = 0, stream=None):
+    """Load a CSR (numpy host arrays, or torch CUDA tensors with GPM_DEVICE_PTRS)."""
+    keep = []
+    if hasattr(offsets, "data_ptr"):  # torch tensor
+        is64 = int(offsets.dtype.itemsize == 8)
+        po, pn = offsets.data_ptr(), (nbrs.data_ptr() if nbrs.numel() else 0)
+        nnz = int(nbrs.numel())
+        nv = int(offsets.numel()) - 1 if n is None else n
+        if offsets.is_cuda:
+            flags |= GPM_DEVICE_PTRS
+        keep = [offsets, nbrs]
+    else:
+        off = np.ascontiguousarray(offsets)
+        if off.dtype not in (np.int64, np.int32):
+            off = off.astype(np.int64)
+        nb = np.ascontiguousarray(nbrs, dtype=np.uint32)
+        is64 = int(off.dtype == np.int64)
+        po, pn = off.ctypes.data, (nb.ctypes.data if len(nb) else 0)
+        nnz = int(len(nb))
+        nv = len(off) - 1 if n is None else n
+        keep = [off, nb]
+    h = ctypes.c_void_p()
+    _check(lib().gpm_load_csr(ctypes.c_void_p(po), is64, ctypes.c_void_p(pn), nv, nnz, flags,
+                              _stream(stream), ctypes.byref(h)))
+    del keep
+    return h
+
+
+def gpm_graph_info(g) -> dict:
+    n, m, d, do = ctypes.c_uint32(), ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib().gpm_graph_info(g, ctypes.byref(n), ctypes.byref(m), ctypes.byref(d),
+                                ctypes.byref(do)))
+    return {"n": n.value, "n_edges": m.value, "max_degree": d.value, "max_out_degree": do.value}
+
+
+def gpm_graph_free(g) -> None:
+    lib().gpm_graph_free(g)
+
+
+def gpm_plan(g, pattern, induced: bool = False, mode: int = GPM_COUNT, opts: dict | None = None,
+             stream=None):
+    if isinstance(pattern, str):
+        pattern = gpm_pattern_named(pattern)
+    o = None
+    if opts:
+        o = gpm_plan_opts()
+        for key, val in opts.items():
+            setattr(o, key, int(val))
+    h = ctypes.c_void_p()
+    _check(lib().gpm_plan(g, ctypes.byref(pattern), int(bool(induced)), mode,
+                          ctypes.byref(o) if o is not None else None, _stream(stream),
+                          ctypes.byref(h)))
+    return h
+
+
+def gpm_plan_info(p) -> dict:
+    nt, k = ctypes.c_uint64(), ctypes.c_uint32()
+    _check(lib().gpm_plan_info(p, ctypes.byref(nt), ctypes.byref(k)))
+    return {"n_tasks": nt.value, "k": k.value}
+
+
+def gpm_count(p, stream=None) -> int:
+    out = ctypes.c_uint64()
+    _check(lib().gpm_count(p, ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def gpm_count_range(p, task_lo: int, task_hi: int, stream=None) -> int:
+    out = ctypes.c_uint64()
+    _check(lib().gpm_count_range(p, task_lo, task_hi, ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def gpm_list(p, capacity: int, out=None, stream=None):
+    """List matches into a device buffer; returns (tensor[n_written, k], n_total, truncated)."""
+    import torch
+    k = gpm_plan_info(p)["k"]
+    if out is None:
+        out = torch.empty((max(capacity, 1), k), dtype=torch.int32, device="cuda")
+    nw, nt = ctypes.c_uint64(), ctypes.c_uint64()
+    st = lib().gpm_list(p, ctypes.c_void_p(out.data_ptr()), capacity, ctypes.byref(nw),
+                        ctypes.byref(nt), _stream(stream))
+    if st not in (GPM_OK, GPM_E_CAPACITY):
+        _check(st)
+    return out[: nw.value], nt.value, st == GPM_E_CAPACITY
+
+
+def gpm_plan_stats(p) -> dict:
+    b, n = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().gpm_plan_stats(p, ctypes.byref(b), ctypes.byref(n)))
+    return {"alg_bytes": b.value, "set_ops": n.value}
+
+
+def gpm_plan_free(p) -> None:
+    lib().gpm_plan_free(p)
+
+
+# ----------------------------------------------------------- conveniences
+
+class Graph:
+    """Owning wrapper: Graph(csr) loads once; .count()/.list() build cached plans."""
+
+    def __init__(self, offsets, nbrs, n=None, flags=0, stream=None):
+        self.handle = gpm_load_csr(offsets, nbrs, n, flags, stream)
+        self._plans = {}
+
+    @classmethod
+    def from_csr(cls, csr, **kw):
+        return cls(csr.offsets, csr.nbrs, csr.n, **kw)
+
+    def info(self):
+        return gpm_graph_info(self.handle)
+
+    def plan(self, pattern, induced=False, mode=GPM_COUNT, opts=None, stream=None):
+        key = (pattern if isinstance(pattern, str) else bytes(pattern), bool(induced), mode,
+               tuple(sorted((opts or {}).items())))
+        if key not in self._plans:
+            self._plans[key] = gpm_plan(self.handle, pattern, induced, mode, opts, stream)
+        return self._plans[key]
+
+    def count(self, pattern, induced=False, opts=None, stream=None) -> int:
+        return gpm_count(self.plan(pattern, induced, GPM_COUNT, opts, stream), stream)
+
+    def list(self, pattern, induced=False, capacity=1 << 20, opts=None, stream=None):
+        return gpm_list(self.plan(pattern, induced, GPM_LIST, opts, stream), capacity, stream=stream)
+
+    def close(self):
+        for p in self._plans.values():
+            gpm_plan_free(p)
+        self._plans.clear()
+        if self.handle:
+            gpm_graph_free(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
