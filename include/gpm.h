@@ -178,17 +178,105 @@ gpm_status gpm_list(gpm_plan_t* p, uint32_t* out_dev, uint64_t capacity, uint64_
 /*
  * Statistics of the plan's last gpm_count / gpm_count_range / gpm_list call,
  * available when the plan was built with collect_stats = 1 (GPM_E_INVALID_ARG
- * otherwise).  alg_bytes sums, over every set operation A∘B of the DFS
- * (Section 6.1), 4 * (min(|A|,|B|) + min(max(|A|,|B|), min(|A|,|B|) *
- * ceil(log2(max(|A|,|B|) + 1)))) bytes of operands (the cheaper of a merge
- * and a binary search), 16 B of list offsets and 4 B per written element, plus
- * 8 B per root task; set_ops counts the set operations.  Both are integers
- * independent of the schedule.
+ * otherwise).  All are integers independent of the schedule.
+ *   alg_bytes  sum over every sorted-set operation A∘B (Section 6.1) of
+ *              4 * (min(|A|,|B|) + min(max(|A|,|B|), min(|A|,|B|) *
+ *              ceil(log2(max(|A|,|B|) + 1)))) operand bytes (the cheaper of a
+ *              merge and a binary search), 16 B of list offsets and 4 B per
+ *              written element, plus 8 B per root task;
+ *   set_ops    number of sorted-set operations of the sorted-set kernels;
+ *   word_ops   bitmap word operations of the local graph search (Section
+ *              5.4 (2), Section 6.2): one per 32-bit AND(+POPC) of two bitmap
+ *              rows and one per single-bit membership test.
+ * Any output pointer may be NULL.
  */
-gpm_status gpm_plan_stats(const gpm_plan_t* p, uint64_t* alg_bytes, uint64_t* set_ops);
+gpm_status gpm_plan_stats(const gpm_plan_t* p, uint64_t* alg_bytes, uint64_t* set_ops,
+                          uint64_t* word_ops);
 
 /* Release the plan.  NULL is ignored. */
 void gpm_plan_free(gpm_plan_t* p);
+
+/* -------------------------------------------------------- motifs, batches */
+
+/*
+ * Vertex-induced k-motif counts of one graph (Section 2.1 k-MC; Section 5.3
+ * multi-pattern fission; Section 5.4 (1) counting-only pruning by pattern
+ * decomposition).  k = 3: out[0..1] = {wedge, triangle}.  k = 4: out[0..5] =
+ * {4-path, 3-star, 4-cycle, tailed-triangle, diamond, 4-clique}.  Only
+ * connected patterns are counted.  `out` is host memory.  Equivalent to a
+ * batch of one graph; synchronises `stream`.
+ */
+gpm_status gpm_motif_count(gpm_graph* g, uint32_t k, uint64_t* out, void* stream);
+
+typedef struct gpm_batch_s gpm_batch_t;
+
+/*
+ * Prepare k-motif counting (k = 3 or 4) over n_graphs resident graphs, run as
+ * one persistent launch per kernel family over a device-side queue of
+ * (graph, root) tasks spanning all graphs, captured once into a CUDA graph.
+ * Builds each graph's DAG and task lists if not cached.  With opts->chunk,
+ * opts->bsearch_ratio and opts->warps_per_block all zero, an autotuner times
+ * candidate task-chunk sizes, intersection thresholds and CTA shapes on the
+ * batch itself and keeps the fastest; nonzero fields fix them.  The graphs
+ * must outlive the batch.  Returns GPM_E_INVALID_ARG for k not in {3, 4} or
+ * n_graphs = 0.
+ */
+gpm_status gpm_batch_create(gpm_graph* const* graphs, uint32_t n_graphs, uint32_t k,
+                            const gpm_plan_opts* opts, void* stream, gpm_batch_t** out);
+
+/* Run the batch: out is host uint64[n_graphs][2 or 6], per graph the counts
+ * in gpm_motif_count's order.  Synchronises `stream`. */
+gpm_status gpm_batch_count(gpm_batch_t* b, uint64_t* out, void* stream);
+
+/* Chosen configuration of a batch (after autotuning): task chunk,
+ * intersection threshold, warps per CTA of the per-edge kernels. */
+gpm_status gpm_batch_info(const gpm_batch_t* b, uint32_t* chunk, uint32_t* bsearch_ratio,
+                          uint32_t* warps_per_block);
+
+/* Release the batch (not its graphs).  NULL is ignored. */
+void gpm_batch_free(gpm_batch_t* b);
+
+/* ---------------------------------------------------------------- serving */
+
+typedef struct gpm_server_s gpm_server_t;
+
+/*
+ * A query server over resident graphs with continuous batching (a serving
+ * extension of Section 7.2 (3) adaptive buffering: a query's device memory is
+ * its plan's DFS buffers, counters and root lists).  Up to max_inflight
+ * queries (1..256) run concurrently on their own streams; a pending query is
+ * admitted, in arrival order, when a slot is free and its memory fits in
+ * mem_budget bytes (a query that does not fit yet is passed over by smaller
+ * ones behind it; one that exceeds the whole budget runs alone when the
+ * server is otherwise idle).  Plans are built on first use and cached per
+ * (graph, pattern, induced).  A scheduler thread polls CUDA events: no
+ * device-side waits.  The graphs must outlive the server and must not be used
+ * through other calls while the server may build plans on them.
+ */
+gpm_status gpm_server_create(size_t mem_budget, uint32_t max_inflight, gpm_server_t** out);
+
+/* Submit a count query; *ticket identifies it.  Thread-safe. */
+gpm_status gpm_server_submit(gpm_server_t* s, gpm_graph* g, const gpm_pattern* pattern,
+                             int induced, uint64_t* ticket);
+
+/* Non-blocking: *done = 1 once the query finished; then *count and
+ * *latency_s (submission to completion, seconds) are written (either may be
+ * NULL) and the query's own status is returned. */
+gpm_status gpm_server_poll(gpm_server_t* s, uint64_t ticket, int* done, uint64_t* count,
+                           double* latency_s);
+
+/* Block until the query finished or timeout_s elapsed (GPM_E_TIMEOUT). */
+gpm_status gpm_server_wait(gpm_server_t* s, uint64_t ticket, double timeout_s, uint64_t* count,
+                           double* latency_s);
+
+/* Counters: completed queries, pending queries, the largest number of
+ * queries in flight at once, device bytes admitted right now. */
+gpm_status gpm_server_stats(gpm_server_t* s, uint64_t* completed, uint64_t* pending,
+                            uint64_t* peak_inflight, size_t* bytes_in_use);
+
+/* Stop the scheduler after in-flight work drains, free plans and streams.
+ * Pending queries are dropped.  NULL is ignored. */
+void gpm_server_free(gpm_server_t* s);
 
 /* ------------------------------------------------------------- errors */
 

@@ -79,7 +79,7 @@ def _L():
         lib.og_count_ranges.restype = ctypes.c_int
         lib.og_count_ranges.argtypes = [i64p, u32p, ctypes.c_uint32, ctypes.c_int, ctypes.c_uint32,
                                         ctypes.c_int, u64p, ctypes.c_uint64, ctypes.c_int, u64p,
-                                        ctypes.POINTER(ctypes.c_double)]
+                                        u64p, ctypes.POINTER(ctypes.c_double)]
         lib.og_list.restype = ctypes.c_int
         lib.og_list.argtypes = [i64p, u32p, ctypes.c_uint32, ctypes.c_int, ctypes.c_uint32,
                                 ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, u32p,
@@ -132,20 +132,26 @@ def count(g, pattern: str, induced: bool = False, task_lo: int = 0, task_hi: int
     return out.value
 
 
-def count_ranges(g, pattern: str, ranges, induced: bool = False,
-                 nthreads: int = 1) -> tuple[int, float]:
-    """O2 count summed over task ranges [(lo, hi), ...]; returns (count, seconds
-    of the counting phase, setup excluded)."""
+def count_ranges(g, pattern: str, ranges, induced: bool = False, nthreads: int = 1,
+                 per_range: bool = False):
+    """O2 counts of task ranges [(lo, hi), ...] with one setup.  Returns
+    (sum, seconds of the counting phase) or, with per_range, (list of counts,
+    seconds)."""
     fam, k, _ = PATTERNS[pattern]
     off, nbr, po, pn = _arrs(g)
     rr = np.asarray(ranges, dtype=np.uint64).reshape(-1)
     if len(rr) == 0:
-        return 0, 0.0
+        return ([] if per_range else 0), 0.0
+    nr = len(rr) // 2
+    each = np.zeros(nr, dtype=np.uint64)
     out = ctypes.c_uint64(0)
     sec = ctypes.c_double(0.0)
     _check(_L().og_count_ranges(po, pn, g.n, fam, k, int(induced),
-                                rr.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), len(rr) // 2,
-                                nthreads, ctypes.byref(out), ctypes.byref(sec)))
+                                rr.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), nr, nthreads,
+                                each.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                ctypes.byref(out), ctypes.byref(sec)))
+    if per_range:
+        return [int(x) for x in each], sec.value
     return out.value, sec.value
 
 

@@ -409,49 +409,53 @@ int og_count(const int64_t* off, const uint32_t* nbr, uint32_t n, int family, ui
 }
 
 /*
- * O2 count summed over several task ranges [ranges[2i], ranges[2i+1]) with one
- * shared setup (orientation, task list).  *seconds receives the wall time of
- * the counting phase only (setup excluded, as preprocessing is excluded from
- * the paper's timings, Section 8).  Returns 0, -1 or -2.
+ * O2 counts of several task ranges [ranges[2i], ranges[2i+1]) with one shared
+ * setup (orientation, task list).  per_range[i] (if not NULL) receives range
+ * i's count and *out their sum; *seconds the wall time of the counting phase
+ * only (setup excluded, as preprocessing is excluded from the paper's
+ * timings, Section 8).  Returns 0, -1 or -2.
  */
 int og_count_ranges(const int64_t* off, const uint32_t* nbr, uint32_t n, int family, uint32_t k,
                     int induced, const uint64_t* ranges, uint64_t nranges, int nthreads,
-                    uint64_t* out, double* seconds) {
+                    uint64_t* per_range, uint64_t* out, double* seconds) {
   og_ctx c;
   int rc = og_ctx_init(&c, off, nbr, n, family, k);
   if (rc) return rc;
   if (nthreads < 1) nthreads = 1;
   struct timespec t0, t1;
   clock_gettime(CLOCK_MONOTONIC, &t0);
-  uint64_t total = 0;
+  uint64_t grand = 0;
   int failed = 0;
+  for (uint64_t r = 0; r < nranges && !failed; r++) {
+    uint64_t lo = ranges[2 * r], hi = ranges[2 * r + 1];
+    if (hi > c.ntasks) hi = c.ntasks;
+    if (lo > hi) lo = hi;
+    uint64_t total = 0;
 #pragma omp parallel num_threads(nthreads) reduction(+ : total)
-  {
-    uint32_t* bufs[8];
-    int ok = 1;
-    for (int i = 0; i < 8; i++) {
-      bufs[i] = (uint32_t*)malloc((c.maxdeg + 1) * sizeof(uint32_t));
-      if (!bufs[i]) ok = 0;
-    }
-    if (!ok) {
+    {
+      uint32_t* bufs[8];
+      int ok = 1;
+      for (int i = 0; i < 8; i++) {
+        bufs[i] = (uint32_t*)malloc((c.maxdeg + 1) * sizeof(uint32_t));
+        if (!bufs[i]) ok = 0;
+      }
+      if (!ok) {
 #pragma omp atomic write
-      failed = 1;
-    } else {
-      for (uint64_t r = 0; r < nranges; r++) {
-        uint64_t lo = ranges[2 * r], hi = ranges[2 * r + 1];
-        if (hi > c.ntasks) hi = c.ntasks;
-        if (lo > hi) lo = hi;
+        failed = 1;
+      } else {
 #pragma omp for schedule(dynamic, 16)
         for (int64_t t = (int64_t)lo; t < (int64_t)hi; t++)
           total += og_task(&c.g, &c.dag, family, k, induced, c.src[t], c.dst[t], bufs, NULL);
       }
+      for (int i = 0; i < 8; i++) free(bufs[i]);
     }
-    for (int i = 0; i < 8; i++) free(bufs[i]);
+    if (per_range) per_range[r] = total;
+    grand += total;
   }
   clock_gettime(CLOCK_MONOTONIC, &t1);
   og_ctx_free(&c);
   if (failed) return -1;
-  *out = total;
+  *out = grand;
   *seconds = (double)(t1.tv_sec - t0.tv_sec) + 1e-9 * (double)(t1.tv_nsec - t0.tv_nsec);
   return 0;
 }

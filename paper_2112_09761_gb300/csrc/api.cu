@@ -29,6 +29,10 @@ cudaError_t lgs_launch_warp(int k, const LgsArgs& a, unsigned blocks, cudaStream
 cudaError_t lgs_launch_block(int k, bool big, bool arc, const LgsArgs& a, unsigned blocks_per_sm,
                              unsigned sms, cudaStream_t s);
 int lgs_block_occupancy(int k, bool big);
+uint32_t wedge_threads();
+cudaError_t degrees32(const DevCsr& g, uint32_t* deg, int sms, cudaStream_t s);
+cudaError_t launch_cycle4_wedge(const DevCsr& g, const uint32_t* deg, uint32_t* cnt, unsigned blocks,
+                                Control* ctl, unsigned long long* stats, cudaStream_t s);
 
 namespace {
 thread_local std::string t_err;
@@ -367,6 +371,7 @@ void gpm_graph_free(gpm_graph* g) {
   cudaFree(g->row_d);
   cudaFree(g->lsrc_d);
   cudaFree(g->ldst_d);
+  cudaFree(g->deg32_d);
   delete g;
 }
 
@@ -463,6 +468,26 @@ gpm_status gpm_plan(gpm_graph* G, const gpm_pattern* pattern, int induced, int m
     p->lgs_mid_bps = (unsigned)lgs_block_occupancy((int)k, false);
     p->lgs_big_bps = (unsigned)lgs_block_occupancy((int)k, true);
   }
+  if (family == kCycle4 && mode == GPM_COUNT && !p->induced && p->count_only && G->g.n) {
+    if (!G->deg32_d) {
+      e = cudaMalloc((void**)&G->deg32_d, (size_t)G->g.n * sizeof(uint32_t));
+      if (e == cudaSuccess) e = degrees32(G->g, G->deg32_d, G->num_sms, s);
+      if (e != cudaSuccess) { cudaFree(G->deg32_d); G->deg32_d = nullptr; gpm_plan_free(p); return cuda_fail(e, "gpm_plan degrees"); }
+    }
+    // one dense counter array (n uint32) per resident CTA, within half of free memory
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const uint64_t per = (uint64_t)G->g.n * sizeof(uint32_t);
+    uint64_t blocks_w = (uint64_t)G->num_sms * 2;
+    blocks_w = std::min<uint64_t>(blocks_w, std::max<uint64_t>(1, (free_b / 2) / per));
+    blocks_w = std::min<uint64_t>(blocks_w, std::max<uint64_t>(1, G->g.n));
+    e = cudaMalloc((void**)&p->wedge_cnt, blocks_w * per);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->wedge_cnt, 0, blocks_w * per, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { gpm_plan_free(p); return cuda_fail(e, "gpm_plan wedge counters"); }
+    p->wedge = true;
+    p->wedge_blocks = (unsigned)blocks_w;
+  }
   e = cudaMalloc((void**)&p->ctl_d, sizeof(Control));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&p->host_pinned, sizeof(Control));
   if (e != cudaSuccess) { gpm_plan_free(p); return cuda_fail(e, "gpm_plan control block"); }
@@ -477,21 +502,59 @@ gpm_status gpm_plan_info(const gpm_plan_t* p, uint64_t* n_tasks, uint32_t* k) {
   return GPM_OK;
 }
 
-static gpm_status run_plan(gpm_plan_t* p, uint64_t lo, uint64_t hi, uint32_t* list_out,
-                           uint64_t cap, cudaStream_t s, Control* res) {
+}  // extern "C"
+
+namespace gpm {
+
+// Enqueue one evaluation of plan p over tasks [lo, hi) on stream s and the
+// copy of its control block to pinned host memory; no synchronisation.
+cudaError_t plan_launch_async(gpm_plan_t* p, uint64_t lo, uint64_t hi, uint32_t* list_out,
+                              uint64_t cap, cudaStream_t s) {
   hi = std::min(hi, p->tasks.count);
   lo = std::min(lo, hi);
   cudaError_t e = cudaMemsetAsync(p->ctl_d, 0, sizeof(Control), s);
-  if (e == cudaSuccess && hi > lo)
-    e = p->lgs ? launch_lgs(p, lo, hi, s) : launch_enum(p, lo, hi, list_out, cap, s);
+  if (e == cudaSuccess && hi > lo) {
+    if (p->wedge && lo == 0 && hi == p->tasks.count)
+      e = launch_cycle4_wedge(p->csr, p->graph->deg32_d, p->wedge_cnt, p->wedge_blocks, p->ctl_d,
+                              p->cfg.stats ? p->ctl_d->stats : nullptr, s);
+    else
+      e = p->lgs ? launch_lgs(p, lo, hi, s) : launch_enum(p, lo, hi, list_out, cap, s);
+  }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(p->host_pinned, p->ctl_d, sizeof(Control), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(e, "enumeration kernel");
+  return e;
+}
+
+// Result of the plan's last evaluation once its stream work has completed.
+gpm_status plan_finish(gpm_plan_t* p, Control* res) {
   memcpy(res, p->host_pinned, sizeof(Control));
   p->last = *res;
   if (res->error & kErrStack) return fail(GPM_E_CUDA, "device check failed: DFS buffer overflow");
   return GPM_OK;
+}
+
+// Device bytes a plan owns for its evaluations (DFS buffers, wedge counters,
+// root lists, control block); the graph's cached structures are not counted.
+size_t plan_exec_bytes(const gpm_plan_t* p) {
+  size_t b = sizeof(Control) + p->gstack_bytes;
+  if (p->wedge) b += (size_t)p->wedge_blocks * p->graph->g.n * sizeof(uint32_t);
+  for (int c = 0; c < 3; c++) b += p->lgs_count[c] * sizeof(uint32_t);
+  b += 2 * p->heavy_count * sizeof(uint64_t);
+  return b;
+}
+
+gpm_status api_fail(gpm_status st, const std::string& msg) { return fail(st, msg); }
+
+}  // namespace gpm
+
+extern "C" {
+
+static gpm_status run_plan(gpm_plan_t* p, uint64_t lo, uint64_t hi, uint32_t* list_out,
+                           uint64_t cap, cudaStream_t s, Control* res) {
+  cudaError_t e = plan_launch_async(p, lo, hi, list_out, cap, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "enumeration kernel");
+  return plan_finish(p, res);
 }
 
 gpm_status gpm_count(gpm_plan_t* p, uint64_t* out_count, void* stream) {
@@ -524,11 +587,13 @@ gpm_status gpm_list(gpm_plan_t* p, uint32_t* out_dev, uint64_t capacity, uint64_
   return GPM_OK;
 }
 
-gpm_status gpm_plan_stats(const gpm_plan_t* p, uint64_t* alg_bytes, uint64_t* set_ops) {
+gpm_status gpm_plan_stats(const gpm_plan_t* p, uint64_t* alg_bytes, uint64_t* set_ops,
+                          uint64_t* word_ops) {
   if (!p) return fail(GPM_E_INVALID_ARG, "gpm_plan_stats: NULL plan");
   if (!p->cfg.stats) return fail(GPM_E_INVALID_ARG, "gpm_plan_stats: plan built without collect_stats");
   if (alg_bytes) *alg_bytes = p->last.stats[0];
   if (set_ops) *set_ops = p->last.stats[1];
+  if (word_ops) *word_ops = p->last.stats[2];
   return GPM_OK;
 }
 
@@ -539,6 +604,7 @@ void gpm_plan_free(gpm_plan_t* p) {
   for (int c = 0; c < 3; c++) cudaFree(p->lgs_verts[c]);
   cudaFree(p->heavy_idx);
   cudaFree(p->overflow_d);
+  cudaFree(p->wedge_cnt);
   if (p->host_pinned) cudaFreeHost(p->host_pinned);
   delete p;
 }

@@ -31,7 +31,7 @@ struct EnumArgs {
   uint32_t levels;     // buffered levels per warp
   uint32_t chunk;      // tasks per queue grab
   uint32_t ratio;      // binary-search vs merge threshold
-  unsigned long long* stats;  // null, or {algorithmic bytes, set operations}
+  unsigned long long* stats;  // null, or {algorithmic bytes, set operations, word-ops}
   const uint64_t* idx;  // null, or: task t is arc idx[t] (counted if in [arc_lo, arc_hi))
   uint64_t arc_lo, arc_hi;
   const unsigned long long* idx_count;  // null, or the device-side length of idx

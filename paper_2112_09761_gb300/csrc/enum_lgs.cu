@@ -57,9 +57,10 @@ __device__ __forceinline__ unsigned long long row_bits64(const uint32_t* __restr
 }
 
 // Number of L-level extensions of candidate set m (uint64 rows), per lane.
-template <int L>
+template <int L, bool ST>
 __device__ __forceinline__ unsigned long long count64(const unsigned long long* rows,
-                                                      unsigned long long m) {
+                                                      unsigned long long m,
+                                                      unsigned long long& wop) {
   if constexpr (L == 0) {
     return (unsigned long long)__popcll(m);
   } else {
@@ -70,13 +71,14 @@ __device__ __forceinline__ unsigned long long count64(const unsigned long long* 
     while (rem) {
       const int j = __ffsll((long long)rem) - 1;
       rem &= rem - 1;
-      t += count64<L - 1>(rows, m & rows[j]);
+      if constexpr (ST) wop += 2;  // one 64-bit AND (+ POPC below) = two word-ops
+      t += count64<L - 1, ST>(rows, m & rows[j], wop);
     }
     return t;
   }
 }
 
-template <int K>
+template <int K, bool ST>
 __global__ void __launch_bounds__(256) k_lgs_warp(LgsArgs a) {
   __shared__ unsigned long long s_rows[8][kWarpMaxD];
   __shared__ unsigned long long s_acc;
@@ -84,7 +86,7 @@ __global__ void __launch_bounds__(256) k_lgs_warp(LgsArgs a) {
   if (threadIdx.x == 0) s_acc = 0;
   __syncthreads();
   unsigned long long* rows = s_rows[wib];
-  unsigned long long acc = 0, stat_b = 0;
+  unsigned long long acc = 0, stat_b = 0, wop = 0;
   for (;;) {
     unsigned long long start = 0;
     if (lane == 0) start = atomicAdd(a.next, 4ull);
@@ -116,13 +118,17 @@ __global__ void __launch_bounds__(256) k_lgs_warp(LgsArgs a) {
       }
       __syncwarp();
       for (uint32_t i = (uint32_t)ia + lane; i < (uint32_t)ib; i += 32)
-        acc += count64<K - 3>(rows, rows[i]);
+        acc += count64<K - 3, ST>(rows, rows[i], wop);
       __syncwarp();
     }
   }
   acc = warp_sum_u64(acc);
   if (lane == 0 && acc) atomicAdd(&s_acc, acc);
   if (a.stats && lane == 0 && stat_b) atomicAdd(&a.stats[0], stat_b);
+  if constexpr (ST) {
+    wop = warp_sum_u64(wop);
+    if (lane == 0 && wop) atomicAdd(&a.stats[2], wop);
+  }
   __syncthreads();
   if (threadIdx.x == 0 && s_acc) atomicAdd(a.result, s_acc);
 }
@@ -189,14 +195,15 @@ __device__ __forceinline__ uint32_t compact_set(uint32_t S, uint16_t* list) {
   return total;
 }
 
-template <int L, int NW>
+template <int L, int NW, bool ST>
 __device__ __forceinline__ unsigned long long f_set(uint32_t S, const uint32_t* rows, uint32_t nw,
-                                                    const WarpScratch& ws);
+                                                    const WarpScratch& ws, unsigned long long& wop);
 
 // f_L(S) for |S| = s <= 64 after compact_set: compressed rows, lane-parallel.
-template <int L, int NW>
+template <int L, int NW, bool ST>
 __device__ __forceinline__ unsigned long long f_small(uint32_t s, const uint32_t* rows,
-                                                      const WarpScratch& ws) {
+                                                      const WarpScratch& ws,
+                                                      unsigned long long& wop) {
   constexpr int STRIDE = NW + 1;
   const uint32_t lane = lane_id();
 #pragma unroll
@@ -209,6 +216,7 @@ __device__ __forceinline__ unsigned long long f_small(uint32_t s, const uint32_t
         const uint32_t py = ws.list[y];
         b |= (unsigned long long)((rj[py >> 5] >> (py & 31)) & 1u) << y;
       }
+      if constexpr (ST) wop += (s > j + 1) ? s - j - 1 : 0;  // bit tests
       ws.cmp[j] = b;
     }
   }
@@ -217,15 +225,15 @@ __device__ __forceinline__ unsigned long long f_small(uint32_t s, const uint32_t
 #pragma unroll
   for (int h = 0; h < 2; h++) {
     const uint32_t j = lane + 32 * h;
-    if (j < s) t += count64<L - 2>(ws.cmp, ws.cmp[j]);
+    if (j < s) t += count64<L - 2, ST>(ws.cmp, ws.cmp[j], wop);
   }
   __syncwarp();
   return t;
 }
 
-template <int L, int NW>
+template <int L, int NW, bool ST>
 __device__ __forceinline__ unsigned long long f_set(uint32_t S, const uint32_t* rows, uint32_t nw,
-                                                    const WarpScratch& ws) {
+                                                    const WarpScratch& ws, unsigned long long& wop) {
   if constexpr (L == 1) {
     return (unsigned long long)__popc(S);
   } else {
@@ -235,7 +243,7 @@ __device__ __forceinline__ unsigned long long f_set(uint32_t S, const uint32_t* 
     if (s < (uint32_t)L) return 0;
     if (s <= 64) {
       compact_set(S, ws.list);
-      return f_small<L, NW>(s, rows, ws);
+      return f_small<L, NW, ST>(s, rows, ws, wop);
     }
     if constexpr (L == 2) {
       // edges inside S: lanes take members x, |S ∩ row_x| word by word
@@ -247,6 +255,7 @@ __device__ __forceinline__ unsigned long long f_set(uint32_t S, const uint32_t* 
         const uint32_t x = ws.list[k];
         const uint32_t* rx = rows + x * STRIDE;
         for (uint32_t w = (x + 1) >> 5; w < nw; w++) acc += __popc(ws.sb[w] & rx[w]);
+        if constexpr (ST) wop += nw - ((x + 1) >> 5);
       }
       __syncwarp();
       return acc;
@@ -261,7 +270,8 @@ __device__ __forceinline__ unsigned long long f_set(uint32_t S, const uint32_t* 
         const int x = wl * 32 + __ffs(word) - 1;
         if ((int)lane == wl) rem &= rem - 1;
         const uint32_t rx = (lane < (uint32_t)NW) ? rows[x * STRIDE + lane] : 0u;
-        t += f_set<L - 1, NW>(S & rx, rows, nw, ws);
+        if constexpr (ST) wop += (lane < nw) ? 1u : 0u;
+        t += f_set<L - 1, NW, ST>(S & rx, rows, nw, ws, wop);
       }
       return t;
     }
@@ -271,7 +281,7 @@ __device__ __forceinline__ unsigned long long f_set(uint32_t S, const uint32_t* 
 // ARC = false: roots are vertices u of a.verts; ARC = true: roots are the
 // arcs a.idx[q] (members N+(u) ∩ N+(v)); roots whose member set exceeds
 // 32*NW are appended to a.overflow for the sorted-set kernel.
-template <int K, int NW, bool ARC>
+template <int K, int NW, bool ARC, bool ST>
 __global__ void __launch_bounds__(kBlockThreads) k_lgs_block(LgsArgs a) {
   using SM = BlockSmem<NW>;
   constexpr int MAXD = SM::MAXD, STRIDE = SM::STRIDE;
@@ -290,7 +300,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_lgs_block(LgsArgs a) {
   ws.list = reinterpret_cast<uint16_t*>(s_raw + SM::list) + wib * MAXD;
   ws.cmp = reinterpret_cast<unsigned long long*>(s_raw + SM::cmp) + wib * 64;
   if (threadIdx.x == 0) s_acc = 0;
-  unsigned long long acc = 0, stat_b = 0;
+  unsigned long long acc = 0, stat_b = 0, wop = 0;
   const uint64_t nroots = ARC ? a.nidx : a.nverts;
   for (;;) {
     __syncthreads();
@@ -414,30 +424,35 @@ __global__ void __launch_bounds__(kBlockThreads) k_lgs_block(LgsArgs a) {
         // root arc (u, member r): K-cliques = (K-2)-cliques inside row_r
         const int64_t id_pos = ridx[r];
         if (id_pos < ia || id_pos >= ib) continue;
-        acc += f_set<K - 2, NW>(m, rows, nw, ws);
+        acc += f_set<K - 2, NW, ST>(m, rows, nw, ws, wop);
       } else {
         // root arc (u, v), third vertex = member r: (K-3)-cliques inside row_r
-        acc += f_set<K - 3, NW>(m, rows, nw, ws);
+        acc += f_set<K - 3, NW, ST>(m, rows, nw, ws, wop);
       }
     }
   }
   acc = warp_sum_u64(acc);
   if (lane == 0 && acc) atomicAdd(&s_acc, acc);
   if (a.stats && lane == 0 && stat_b) atomicAdd(&a.stats[0], stat_b);
+  if constexpr (ST) {
+    wop = warp_sum_u64(wop);
+    if (lane == 0 && wop) atomicAdd(&a.stats[2], wop);
+  }
   __syncthreads();
   if (threadIdx.x == 0 && s_acc) atomicAdd(a.result, s_acc);
 }
 
 template <int K>
 cudaError_t launch_warp_k(const LgsArgs& a, unsigned blocks, cudaStream_t s) {
-  k_lgs_warp<K><<<blocks, 256, 0, s>>>(a);
+  if (a.stats) k_lgs_warp<K, true><<<blocks, 256, 0, s>>>(a);
+  else k_lgs_warp<K, false><<<blocks, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int K, int NW, bool ARC>
 cudaError_t launch_block_k(const LgsArgs& a, unsigned blocks, cudaStream_t s) {
   const size_t smem = BlockSmem<NW>::bytes;
-  auto kern = k_lgs_block<K, NW, ARC>;
+  auto kern = a.stats ? k_lgs_block<K, NW, ARC, true> : k_lgs_block<K, NW, ARC, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<blocks, kBlockThreads, smem, s>>>(a);
@@ -447,7 +462,7 @@ cudaError_t launch_block_k(const LgsArgs& a, unsigned blocks, cudaStream_t s) {
 template <int K, int NW>
 int occ_block_k() {
   const size_t smem = BlockSmem<NW>::bytes;
-  auto kern = k_lgs_block<K, NW, false>;
+  auto kern = k_lgs_block<K, NW, false, false>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 1;
   int b = 0;

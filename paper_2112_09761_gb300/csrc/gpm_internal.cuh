@@ -47,7 +47,7 @@ struct Control {
   unsigned long long next;       // dynamic task queue head (relative to task_lo)
   unsigned long long result;     // match count accumulator
   unsigned long long list_head;  // listing cursor (matches reserved so far)
-  unsigned long long stats[2];   // algorithmic bytes, set operations (if collected)
+  unsigned long long stats[3];   // algorithmic bytes, set operations, bitmap word-ops
   unsigned long long overflow;   // arcs appended to the plan's overflow list
   unsigned int error;            // nonzero: a device-side check failed
   unsigned int pad;
@@ -89,6 +89,7 @@ struct gpm_graph {
   uint32_t* lsrc_d = nullptr;
   uint32_t* ldst_d = nullptr;
   uint64_t lower_count = 0;
+  uint32_t* deg32_d = nullptr;  // undirected degree of every vertex (lazily built)
   int device = 0;
   int num_sms = 0;
 };
@@ -116,6 +117,10 @@ struct gpm_plan_s {
   uint64_t* heavy_idx = nullptr;  // arcs of roots with d > 1024 (arc-rooted local graphs)
   uint64_t heavy_count = 0;
   uint64_t* overflow_d = nullptr;  // heavy arcs whose local graph exceeds 1024 members
+  // counting-only 4-cycles (full counts): per-CTA dense wedge counters
+  bool wedge = false;
+  uint32_t* wedge_cnt = nullptr;
+  unsigned wedge_blocks = 0;
   unsigned lgs_warp_blocks = 0, lgs_mid_bps = 1, lgs_big_bps = 1;
 };
 

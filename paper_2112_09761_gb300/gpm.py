@@ -81,11 +81,29 @@ def lib():
         L.gpm_count.argtypes = [vp, u64p, vp]
         L.gpm_count_range.argtypes = [vp, u64, u64, u64p, vp]
         L.gpm_list.argtypes = [vp, vp, u64, u64p, u64p, vp]
-        L.gpm_plan_stats.argtypes = [vp, u64p, u64p]
+        L.gpm_plan_stats.argtypes = [vp, u64p, u64p, u64p]
+        L.gpm_motif_count.argtypes = [vp, u32, u64p, vp]
+        L.gpm_batch_create.argtypes = [ctypes.POINTER(vp), u32, u32, ctypes.POINTER(gpm_plan_opts),
+                                       vp, ctypes.POINTER(vp)]
+        L.gpm_batch_count.argtypes = [vp, u64p, vp]
+        L.gpm_batch_info.argtypes = [vp, u32p, u32p, u32p]
+        L.gpm_batch_free.argtypes = [vp]
+        L.gpm_batch_free.restype = None
+        L.gpm_server_create.argtypes = [ctypes.c_size_t, u32, ctypes.POINTER(vp)]
+        L.gpm_server_submit.argtypes = [vp, vp, ctypes.POINTER(gpm_pattern), ctypes.c_int, u64p]
+        L.gpm_server_poll.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_int), u64p,
+                                      ctypes.POINTER(ctypes.c_double)]
+        L.gpm_server_wait.argtypes = [vp, u64, ctypes.c_double, u64p, ctypes.POINTER(ctypes.c_double)]
+        L.gpm_server_stats.argtypes = [vp, u64p, u64p, u64p, ctypes.POINTER(ctypes.c_size_t)]
+        L.gpm_server_free.argtypes = [vp]
+        L.gpm_server_free.restype = None
         L.gpm_plan_free.argtypes = [vp]
         L.gpm_plan_free.restype = None
         for name in ("gpm_pattern_named", "gpm_load_csr", "gpm_graph_info", "gpm_plan",
-                     "gpm_plan_info", "gpm_count", "gpm_count_range", "gpm_list", "gpm_plan_stats"):
+                     "gpm_plan_info", "gpm_count", "gpm_count_range", "gpm_list", "gpm_plan_stats",
+                     "gpm_motif_count", "gpm_batch_create", "gpm_batch_count", "gpm_batch_info",
+                     "gpm_server_create", "gpm_server_submit", "gpm_server_poll",
+                     "gpm_server_wait", "gpm_server_stats"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -230,9 +248,100 @@ def gpm_list(p, capacity: int, out=None, stream=None):
 
 
 def gpm_plan_stats(p) -> dict:
-    b, n = ctypes.c_uint64(), ctypes.c_uint64()
-    _check(lib().gpm_plan_stats(p, ctypes.byref(b), ctypes.byref(n)))
-    return {"alg_bytes": b.value, "set_ops": n.value}
+    b, n, w = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().gpm_plan_stats(p, ctypes.byref(b), ctypes.byref(n), ctypes.byref(w)))
+    return {"alg_bytes": b.value, "set_ops": n.value, "word_ops": w.value}
+
+
+MOTIF3 = ["wedge", "triangle"]
+MOTIF4 = ["4-path", "3-star", "4-cycle", "tailed-triangle", "diamond", "4-clique"]
+
+
+def gpm_motif_count(g, k: int, stream=None) -> list[int]:
+    """Vertex-induced k-motif counts (k = 3: MOTIF3 order, k = 4: MOTIF4 order)."""
+    w = 2 if k == 3 else 6
+    out = (ctypes.c_uint64 * w)()
+    _check(lib().gpm_motif_count(g, k, out, _stream(stream)))
+    return [int(x) for x in out]
+
+
+def _opts(opts):
+    if not opts:
+        return None
+    o = gpm_plan_opts()
+    for key, val in opts.items():
+        setattr(o, key, int(val))
+    return o
+
+
+def gpm_batch_create(graphs, k: int, opts: dict | None = None, stream=None):
+    arr = (ctypes.c_void_p * len(graphs))(*[ctypes.c_void_p(getattr(h, "value", h)) for h in graphs])
+    o = _opts(opts)
+    h = ctypes.c_void_p()
+    _check(lib().gpm_batch_create(arr, len(graphs), k, ctypes.byref(o) if o is not None else None,
+                                  _stream(stream), ctypes.byref(h)))
+    h._n = len(graphs)
+    h._k = k
+    return h
+
+
+def gpm_batch_count(b, stream=None) -> np.ndarray:
+    w = 2 if b._k == 3 else 6
+    out = np.zeros((b._n, w), dtype=np.uint64)
+    _check(lib().gpm_batch_count(b, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                 _stream(stream)))
+    return out
+
+
+def gpm_batch_info(b) -> dict:
+    c, r, w = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib().gpm_batch_info(b, ctypes.byref(c), ctypes.byref(r), ctypes.byref(w)))
+    return {"chunk": c.value, "bsearch_ratio": r.value, "warps_per_block": w.value}
+
+
+def gpm_batch_free(b) -> None:
+    lib().gpm_batch_free(b)
+
+
+def gpm_server_create(mem_budget: int, max_inflight: int = 8):
+    h = ctypes.c_void_p()
+    _check(lib().gpm_server_create(mem_budget, max_inflight, ctypes.byref(h)))
+    return h
+
+
+def gpm_server_submit(srv, g, pattern, induced: bool = False) -> int:
+    if isinstance(pattern, str):
+        pattern = gpm_pattern_named(pattern)
+    t = ctypes.c_uint64()
+    _check(lib().gpm_server_submit(srv, g, ctypes.byref(pattern), int(bool(induced)),
+                                   ctypes.byref(t)))
+    return t.value
+
+
+def gpm_server_poll(srv, ticket: int):
+    """(done, count, latency_s) — count/latency are None while running."""
+    d, c, l = ctypes.c_int(), ctypes.c_uint64(), ctypes.c_double()
+    _check(lib().gpm_server_poll(srv, ticket, ctypes.byref(d), ctypes.byref(c), ctypes.byref(l)))
+    return (True, c.value, l.value) if d.value else (False, None, None)
+
+
+def gpm_server_wait(srv, ticket: int, timeout_s: float = 600.0):
+    """(count, latency_s)."""
+    c, l = ctypes.c_uint64(), ctypes.c_double()
+    _check(lib().gpm_server_wait(srv, ticket, timeout_s, ctypes.byref(c), ctypes.byref(l)))
+    return c.value, l.value
+
+
+def gpm_server_stats(srv) -> dict:
+    c, p, pk, b = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_size_t()
+    _check(lib().gpm_server_stats(srv, ctypes.byref(c), ctypes.byref(p), ctypes.byref(pk),
+                                  ctypes.byref(b)))
+    return {"completed": c.value, "pending": p.value, "peak_inflight": pk.value,
+            "bytes_in_use": b.value}
+
+
+def gpm_server_free(srv) -> None:
+    lib().gpm_server_free(srv)
 
 
 def gpm_plan_free(p) -> None:
