@@ -278,6 +278,30 @@ gpm_status gpm_server_stats(gpm_server_t* s, uint64_t* completed, uint64_t* pend
  * Pending queries are dropped.  NULL is ignored. */
 void gpm_server_free(gpm_server_t* s);
 
+/* ------------------------------------------------- allocation-free count */
+
+/*
+ * Triangle count of an undirected graph whose CSR is already in device memory,
+ * for callers that must not allocate device memory (loops where cudaMalloc /
+ * cudaFree could synchronise the device and stall other streams; plug-ins
+ * whose host application owns all device memory; processes that reserve all
+ * their device memory up front).  The paper has no counterpart to this entry
+ * point: it is a service of this library.
+ *   offsets_dev  int64[n+1] device row offsets; nbrs_dev uint32 device
+ *                neighbour lists (sorted ascending, both directions, no loops
+ *                or duplicates; not validated here; may be NULL when the graph
+ *                has no edges)
+ *   count_dev    device uint64 that receives the count (written last)
+ *   stream       enqueued on `stream`; the call does not synchronise it
+ * No memory is allocated: all working memory is one fixed 1 MiB device array
+ * in the library, so n may be at most 131,069 (GPM_E_INVALID_ARG beyond).
+ * The first call on a device looks the array up for that device; make that
+ * first call before any stream capture.  Calls share the array: calls that
+ * overlap on the GPU (for example on two streams) race; serialise them.
+ */
+gpm_status gpm_count_triangles_noalloc(const int64_t* offsets_dev, const uint32_t* nbrs_dev,
+                                       uint32_t n, uint64_t* count_dev, void* stream);
+
 /* ------------------------------------------------------------- errors */
 
 /* Description of the last error on this host thread ("" if none). */

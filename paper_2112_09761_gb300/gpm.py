@@ -97,13 +97,14 @@ def lib():
         L.gpm_server_stats.argtypes = [vp, u64p, u64p, u64p, ctypes.POINTER(ctypes.c_size_t)]
         L.gpm_server_free.argtypes = [vp]
         L.gpm_server_free.restype = None
+        L.gpm_count_triangles_noalloc.argtypes = [vp, vp, u32, vp, vp]
         L.gpm_plan_free.argtypes = [vp]
         L.gpm_plan_free.restype = None
         for name in ("gpm_pattern_named", "gpm_load_csr", "gpm_graph_info", "gpm_plan",
                      "gpm_plan_info", "gpm_count", "gpm_count_range", "gpm_list", "gpm_plan_stats",
                      "gpm_motif_count", "gpm_batch_create", "gpm_batch_count", "gpm_batch_info",
                      "gpm_server_create", "gpm_server_submit", "gpm_server_poll",
-                     "gpm_server_wait", "gpm_server_stats"):
+                     "gpm_server_wait", "gpm_server_stats", "gpm_count_triangles_noalloc"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -342,6 +343,15 @@ def gpm_server_stats(srv) -> dict:
 
 def gpm_server_free(srv) -> None:
     lib().gpm_server_free(srv)
+
+
+def gpm_count_triangles_noalloc(offsets_dev, nbrs_dev, n: int, count_dev, stream=None) -> None:
+    """Triangle count into count_dev (device tensors in, device tensor out); the
+    library allocates nothing for it.  Enqueued on the stream, not synchronised."""
+    _check(lib().gpm_count_triangles_noalloc(
+        ctypes.c_void_p(offsets_dev.data_ptr()),
+        ctypes.c_void_p(nbrs_dev.data_ptr() if nbrs_dev.numel() else 0), n,
+        ctypes.c_void_p(count_dev.data_ptr()), _stream(stream)))
 
 
 def gpm_plan_free(p) -> None:
