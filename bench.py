@@ -42,6 +42,9 @@ WORKLOADS = {
                "desc": "Erdos-Renyi G(n=10000, m=80000), seed 1"},
     "chunglu-1m": {"patterns": ["diamond", "4-cycle"], "induced": False,
                    "desc": "Chung-Lu n=1e6, 32M endpoint pairs, gamma 2.1, seed 3"},
+    # small case of the default workload's dominant kernel, for ncu captures
+    "rmat20": {"patterns": ["5-clique"], "induced": False,
+               "desc": "R-MAT scale 20, edge factor 16, (0.57,0.19,0.19,0.05), seed 20"},
 }
 
 
@@ -288,7 +291,7 @@ def main():
     off_h = torch.from_numpy(g.offsets).pin_memory()
     nbr_h = torch.from_numpy(g.nbrs.view(np.int32)).pin_memory()
     e2e_times = []
-    for i in range(args.e2e_steps + 1):
+    for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         barrier()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)

@@ -23,12 +23,11 @@ cudaError_t occupancy_small(int family, bool induced, bool list, bool co, int th
                             int* blocks, int* regs);
 cudaError_t widen_offsets(const int32_t* in, uint64_t count, int64_t* out, cudaStream_t s);
 uint32_t lgs_warp_max_degree();
-uint32_t lgs_block_mid_degree();
 uint32_t lgs_block_max_degree();
 cudaError_t lgs_launch_warp(int k, const LgsArgs& a, unsigned blocks, cudaStream_t s);
-cudaError_t lgs_launch_block(int k, bool big, bool arc, const LgsArgs& a, unsigned blocks_per_sm,
+cudaError_t lgs_launch_block(int k, int nw, bool arc, const LgsArgs& a, unsigned blocks_per_sm,
                              unsigned sms, cudaStream_t s);
-int lgs_block_occupancy(int k, bool big);
+int lgs_block_occupancy(int k, int nw);
 uint32_t wedge_threads();
 cudaError_t degrees32(const DevCsr& g, uint32_t* deg, int sms, cudaStream_t s);
 cudaError_t launch_cycle4_wedge(const DevCsr& g, const uint32_t* deg, uint32_t* cnt, unsigned blocks,
@@ -207,14 +206,15 @@ cudaError_t launch_lgs(gpm_plan_t* p, uint64_t lo, uint64_t hi, cudaStream_t s) 
   la.overflow = p->overflow_d;
   la.overflow_count = &p->ctl_d->overflow;
   cudaError_t e = cudaSuccess;
-  for (int c = 0; c < 3 && e == cudaSuccess; c++) {
+  static const int kClassWords[4] = {0, 8, 16, 32};
+  for (int c = 0; c < 4 && e == cudaSuccess; c++) {
     if (!p->lgs_count[c]) continue;
     la.verts = p->lgs_verts[c];
     la.nverts = p->lgs_count[c];
     e = cudaMemsetAsync(&p->ctl_d->next, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) break;
     if (c == 0) e = lgs_launch_warp((int)p->k, la, p->lgs_warp_blocks, s);
-    else e = lgs_launch_block((int)p->k, c == 2, false, la, c == 2 ? p->lgs_big_bps : p->lgs_mid_bps,
+    else e = lgs_launch_block((int)p->k, kClassWords[c], false, la, p->lgs_bps[c],
                               (unsigned)G->num_sms, s);
   }
   if (e == cudaSuccess && p->heavy_count) {
@@ -224,7 +224,7 @@ cudaError_t launch_lgs(gpm_plan_t* p, uint64_t lo, uint64_t hi, cudaStream_t s) 
     la.nidx = p->heavy_count;
     e = cudaMemsetAsync(&p->ctl_d->next, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess)
-      e = lgs_launch_block((int)p->k, true, true, la, p->lgs_big_bps, (unsigned)G->num_sms, s);
+      e = lgs_launch_block((int)p->k, 32, true, la, p->lgs_bps[3], (unsigned)G->num_sms, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(&p->ctl_d->next, 0, sizeof(unsigned long long), s);
     EnumArgs a{};
     a.g = p->csr;
@@ -455,8 +455,8 @@ gpm_status gpm_plan(gpm_graph* G, const gpm_pattern* pattern, int induced, int m
   }
   if (family == kClique && mode == GPM_COUNT && k >= 4 && !o.no_lgs) {
     p->lgs = true;
-    e = build_lgs_classes(G, k - 1, lgs_warp_max_degree(), lgs_block_mid_degree(),
-                          lgs_block_max_degree(), p->lgs_verts, p->lgs_count, &p->heavy_idx,
+    const uint32_t bounds[4] = {lgs_warp_max_degree(), 256, 512, lgs_block_max_degree()};
+    e = build_lgs_classes(G, k - 1, bounds, 4, p->lgs_verts, p->lgs_count, &p->heavy_idx,
                           &p->heavy_count, s);
     if (e != cudaSuccess) { gpm_plan_free(p); return cuda_fail(e, "gpm_plan local graph classes"); }
     if (p->heavy_count) {
@@ -465,8 +465,9 @@ gpm_status gpm_plan(gpm_graph* G, const gpm_pattern* pattern, int induced, int m
     }
     p->lgs_warp_blocks = (unsigned)std::min<uint64_t>(
         (uint64_t)G->num_sms * 8, std::max<uint64_t>(1, (p->lgs_count[0] + 7) / 8));
-    p->lgs_mid_bps = (unsigned)lgs_block_occupancy((int)k, false);
-    p->lgs_big_bps = (unsigned)lgs_block_occupancy((int)k, true);
+    p->lgs_bps[1] = (unsigned)lgs_block_occupancy((int)k, 8);
+    p->lgs_bps[2] = (unsigned)lgs_block_occupancy((int)k, 16);
+    p->lgs_bps[3] = (unsigned)lgs_block_occupancy((int)k, 32);
   }
   if (family == kCycle4 && mode == GPM_COUNT && !p->induced && p->count_only && G->g.n) {
     if (!G->deg32_d) {
@@ -538,7 +539,7 @@ gpm_status plan_finish(gpm_plan_t* p, Control* res) {
 size_t plan_exec_bytes(const gpm_plan_t* p) {
   size_t b = sizeof(Control) + p->gstack_bytes;
   if (p->wedge) b += (size_t)p->wedge_blocks * p->graph->g.n * sizeof(uint32_t);
-  for (int c = 0; c < 3; c++) b += p->lgs_count[c] * sizeof(uint32_t);
+  for (int c = 0; c < 4; c++) b += p->lgs_count[c] * sizeof(uint32_t);
   b += 2 * p->heavy_count * sizeof(uint64_t);
   return b;
 }
@@ -601,7 +602,7 @@ void gpm_plan_free(gpm_plan_t* p) {
   if (!p) return;
   cudaFree(p->ctl_d);
   cudaFree(p->gstack_d);
-  for (int c = 0; c < 3; c++) cudaFree(p->lgs_verts[c]);
+  for (int c = 0; c < 4; c++) cudaFree(p->lgs_verts[c]);
   cudaFree(p->heavy_idx);
   cudaFree(p->overflow_d);
   cudaFree(p->wedge_cnt);

@@ -150,22 +150,35 @@ __global__ void __launch_bounds__(256) k_lgs_warp(LgsArgs a) {
 // (one uint64 row per member, in shared memory) and finished lane-parallel,
 // one lane per member; larger sets iterate their members warp-cooperatively.
 
-constexpr int kBlockThreads = 512;
-constexpr int kBlockWarps = kBlockThreads / 32;
+// CTA shape per class: NW words per row (members <= 32*NW); 512 threads for
+// the 8- and 16-word classes (several CTAs per SM), 1024 for the 32-word class
+// (one CTA fills the shared memory, so it brings all the warps).
+template <int NW>
+struct BlockShape {
+  static constexpr int THREADS = NW >= 32 ? 1024 : 512;
+  static constexpr int WARPS = THREADS / 32;
+};
 
 template <int NW>
 struct BlockSmem {
   static constexpr int MAXD = 32 * NW;
   static constexpr int STRIDE = NW + 1;
-  static constexpr size_t rows = 0;                                          // u32 [MAXD*STRIDE]
-  static constexpr size_t key = rows + sizeof(uint32_t) * MAXD * STRIDE;     // u64 [MAXD]
-  static constexpr size_t aid = key + sizeof(unsigned long long) * MAXD;     // u32 [MAXD] ids (id order)
-  static constexpr size_t ridx = aid + sizeof(uint32_t) * MAXD;              // u32 [MAXD] id pos of rank pos
-  static constexpr size_t rpos = ridx + sizeof(uint32_t) * MAXD;             // u32 [MAXD] rank pos of id pos
-  static constexpr size_t cmp = rpos + sizeof(uint32_t) * MAXD;              // u64 [warps][64]
-  static constexpr size_t sbuf = cmp + sizeof(unsigned long long) * 64 * kBlockWarps;  // u32 [warps][32]
-  static constexpr size_t list = sbuf + sizeof(uint32_t) * 32 * kBlockWarps;  // u16 [warps][MAXD]
-  static constexpr size_t bytes = list + sizeof(uint16_t) * MAXD * kBlockWarps;
+  static constexpr int WARPS = BlockShape<NW>::WARPS;
+  static constexpr size_t rows = 0;                                           // u32 [MAXD*STRIDE]
+  static constexpr size_t aid = rows + sizeof(uint32_t) * MAXD * STRIDE;      // u32 [MAXD] ids (id order)
+  static constexpr size_t ridx = aid + sizeof(uint32_t) * MAXD;               // u16 [MAXD] id pos of rank pos
+  static constexpr size_t rpos = ridx + sizeof(uint16_t) * MAXD;              // u16 [MAXD] rank pos of id pos
+  // per-warp scratch; the rank-sort keys (u64 [MAXD]) reuse this area before
+  // the counting phase starts
+  static constexpr size_t scratch = rpos + sizeof(uint16_t) * MAXD;
+  static constexpr size_t cmp = scratch;                                       // u64 [warps][64]
+  static constexpr size_t sbuf = cmp + sizeof(unsigned long long) * 64 * WARPS;  // u32 [warps][32]
+  static constexpr size_t list = sbuf + sizeof(uint32_t) * 32 * WARPS;        // u16 [warps][MAXD]
+  static constexpr size_t scratch_end = list + sizeof(uint16_t) * MAXD * WARPS;
+  static constexpr size_t key = scratch;                                       // u64 [MAXD] (aliases)
+  static constexpr size_t bytes =
+      scratch_end > key + sizeof(unsigned long long) * MAXD ? scratch_end
+                                                            : key + sizeof(unsigned long long) * MAXD;
 };
 
 struct WarpScratch {
@@ -282,15 +295,16 @@ __device__ __forceinline__ unsigned long long f_set(uint32_t S, const uint32_t* 
 // arcs a.idx[q] (members N+(u) ∩ N+(v)); roots whose member set exceeds
 // 32*NW are appended to a.overflow for the sorted-set kernel.
 template <int K, int NW, bool ARC, bool ST>
-__global__ void __launch_bounds__(kBlockThreads) k_lgs_block(LgsArgs a) {
+__global__ void __launch_bounds__(BlockShape<NW>::THREADS) k_lgs_block(LgsArgs a) {
   using SM = BlockSmem<NW>;
+  constexpr int kWarps = BlockShape<NW>::WARPS;
   constexpr int MAXD = SM::MAXD, STRIDE = SM::STRIDE;
   extern __shared__ __align__(16) unsigned char s_raw[];
   uint32_t* rows = reinterpret_cast<uint32_t*>(s_raw + SM::rows);
   unsigned long long* key = reinterpret_cast<unsigned long long*>(s_raw + SM::key);
   uint32_t* aid = reinterpret_cast<uint32_t*>(s_raw + SM::aid);
-  uint32_t* ridx = reinterpret_cast<uint32_t*>(s_raw + SM::ridx);
-  uint32_t* rpos = reinterpret_cast<uint32_t*>(s_raw + SM::rpos);
+  uint16_t* ridx = reinterpret_cast<uint16_t*>(s_raw + SM::ridx);
+  uint16_t* rpos = reinterpret_cast<uint16_t*>(s_raw + SM::rpos);
   __shared__ unsigned long long s_q;
   __shared__ unsigned int s_arc, s_d;
   __shared__ unsigned long long s_acc;
@@ -349,7 +363,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_lgs_block(LgsArgs a) {
       } else {
         key[t] = ~0ull;
       }
-      ridx[t] = t;
+      ridx[t] = (uint16_t)t;
     }
     for (uint32_t t = threadIdx.x; t < d * STRIDE; t += blockDim.x) rows[t] = 0u;
     __syncthreads();
@@ -365,17 +379,17 @@ __global__ void __launch_bounds__(kBlockThreads) k_lgs_block(LgsArgs a) {
             const unsigned long long kt = key[t], kx = key[x];
             if ((kt > kx) == up) {
               key[t] = kx; key[x] = kt;
-              const uint32_t r = ridx[t]; ridx[t] = ridx[x]; ridx[x] = r;
+              const uint16_t r = ridx[t]; ridx[t] = ridx[x]; ridx[x] = r;
             }
           }
         }
         __syncthreads();
       }
     }
-    for (uint32_t t = threadIdx.x; t < d; t += blockDim.x) rpos[ridx[t]] = t;
+    for (uint32_t t = threadIdx.x; t < d; t += blockDim.x) rpos[ridx[t]] = (uint16_t)t;
     __syncthreads();
     // rows in rank order: one warp per member
-    for (uint32_t i = wib; i < d; i += kBlockWarps) {
+    for (uint32_t i = wib; i < d; i += kWarps) {
       const uint32_t v = aid[ridx[i]];
       const int64_t vs = a.dag.off[v];
       const uint32_t dl = (uint32_t)(a.dag.off[v + 1] - vs);
@@ -455,7 +469,7 @@ cudaError_t launch_block_k(const LgsArgs& a, unsigned blocks, cudaStream_t s) {
   auto kern = a.stats ? k_lgs_block<K, NW, ARC, true> : k_lgs_block<K, NW, ARC, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<blocks, kBlockThreads, smem, s>>>(a);
+  kern<<<blocks, BlockShape<NW>::THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -466,7 +480,8 @@ int occ_block_k() {
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 1;
   int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kBlockThreads, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, BlockShape<NW>::THREADS, smem) !=
+      cudaSuccess)
     return 1;
   return b > 0 ? b : 1;
 }
@@ -476,7 +491,6 @@ int occ_block_k() {
 // Size classes handled by the bitmap kernels.
 uint32_t lgs_warp_max_degree() { return kWarpMaxD; }
 uint32_t lgs_block_max_degree() { return 1024; }
-uint32_t lgs_block_mid_degree() { return 256; }
 
 // Launch the warp kernel (d <= 64) for clique size k.
 cudaError_t lgs_launch_warp(int k, const LgsArgs& a, unsigned blocks, cudaStream_t s) {
@@ -490,15 +504,16 @@ cudaError_t lgs_launch_warp(int k, const LgsArgs& a, unsigned blocks, cudaStream
   }
 }
 
-// Launch the block kernel; `big` selects rows of 32 words (d <= 1024) over
-// 8 words (d <= 256); `arc` roots at the arcs of a.idx instead of vertices.
-cudaError_t lgs_launch_block(int k, bool big, bool arc, const LgsArgs& a, unsigned blocks_per_sm,
+// Launch the block kernel with rows of nw words (8: d <= 256, 16: d <= 512,
+// 32: d <= 1024); `arc` roots at the arcs of a.idx (32-word rows).
+cudaError_t lgs_launch_block(int k, int nw, bool arc, const LgsArgs& a, unsigned blocks_per_sm,
                              unsigned sms, cudaStream_t s) {
 #define GPM_B(KK)                                                                            \
   case KK:                                                                                   \
     if (arc) return launch_block_k<KK, 32, true>(a, blocks_per_sm * sms, s);                 \
-    return big ? launch_block_k<KK, 32, false>(a, blocks_per_sm * sms, s)                    \
-               : launch_block_k<KK, 8, false>(a, blocks_per_sm * sms, s);
+    if (nw == 8) return launch_block_k<KK, 8, false>(a, blocks_per_sm * sms, s);             \
+    if (nw == 16) return launch_block_k<KK, 16, false>(a, blocks_per_sm * sms, s);           \
+    return launch_block_k<KK, 32, false>(a, blocks_per_sm * sms, s);
   switch (k) {
     GPM_B(4) GPM_B(5) GPM_B(6) GPM_B(7) GPM_B(8)
     default: return cudaErrorInvalidValue;
@@ -506,9 +521,9 @@ cudaError_t lgs_launch_block(int k, bool big, bool arc, const LgsArgs& a, unsign
 #undef GPM_B
 }
 
-int lgs_block_occupancy(int k, bool big) {
+int lgs_block_occupancy(int k, int nw) {
 #define GPM_O(KK) \
-  case KK: return big ? occ_block_k<KK, 32>() : occ_block_k<KK, 8>();
+  case KK: return nw == 8 ? occ_block_k<KK, 8>() : nw == 16 ? occ_block_k<KK, 16>() : occ_block_k<KK, 32>();
   switch (k) {
     GPM_O(4) GPM_O(5) GPM_O(6) GPM_O(7) GPM_O(8)
     default: return 1;

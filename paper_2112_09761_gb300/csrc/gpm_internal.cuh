@@ -112,8 +112,9 @@ struct gpm_plan_s {
   gpm::Control last{};                  // control block of the last launch
   // local graph search (cliques, counting): root vertices by out-degree class
   bool lgs = false;
-  uint32_t* lgs_verts[3] = {nullptr, nullptr, nullptr};  // d<=64, <=256, <=1024
-  uint64_t lgs_count[3] = {0, 0, 0};
+  // root classes by DAG out-degree: <= 64 (warp), <= 256, <= 512, <= 1024 (CTA)
+  uint32_t* lgs_verts[4] = {nullptr, nullptr, nullptr, nullptr};
+  uint64_t lgs_count[4] = {0, 0, 0, 0};
   uint64_t* heavy_idx = nullptr;  // arcs of roots with d > 1024 (arc-rooted local graphs)
   uint64_t heavy_count = 0;
   uint64_t* overflow_d = nullptr;  // heavy arcs whose local graph exceeds 1024 members
@@ -121,7 +122,8 @@ struct gpm_plan_s {
   bool wedge = false;
   uint32_t* wedge_cnt = nullptr;
   unsigned wedge_blocks = 0;
-  unsigned lgs_warp_blocks = 0, lgs_mid_bps = 1, lgs_big_bps = 1;
+  unsigned lgs_warp_blocks = 0;
+  unsigned lgs_bps[4] = {1, 1, 1, 1};  // resident CTAs per SM of each CTA class
 };
 
 namespace gpm {
@@ -138,10 +140,11 @@ cudaError_t validate_csr(const DevCsr& g, bool full, cudaStream_t stream, unsign
 cudaError_t build_dag(gpm_graph* G, cudaStream_t stream);
 cudaError_t build_rows(gpm_graph* G, cudaStream_t stream);
 cudaError_t build_lower(gpm_graph* G, cudaStream_t stream);
-// Root vertices of the local graph search by DAG out-degree class:
-// [kmin, b0], (b0, b1], (b1, b2]; arcs of roots with out-degree > b2.
-cudaError_t build_lgs_classes(gpm_graph* G, uint32_t kmin, uint32_t b0, uint32_t b1, uint32_t b2,
-                              uint32_t* verts[3], uint64_t counts[3], uint64_t** heavy,
+// Root vertices of the local graph search by DAG out-degree class c:
+// out-degree in (bounds[c-1], bounds[c]] (bounds[-1] = 0) and >= kmin, for
+// c < nclass; and the arcs of roots with out-degree > bounds[nclass-1].
+cudaError_t build_lgs_classes(gpm_graph* G, uint32_t kmin, const uint32_t* bounds, int nclass,
+                              uint32_t** verts, uint64_t* counts, uint64_t** heavy,
                               uint64_t* heavy_count, cudaStream_t stream);
 
 // Enumeration launch (enum.cu).  Runs tasks [lo, hi) of plan p on `stream`.

@@ -401,8 +401,8 @@ cudaError_t build_rows(gpm_graph* G, cudaStream_t s) {
   return e;
 }
 
-cudaError_t build_lgs_classes(gpm_graph* G, uint32_t kmin, uint32_t b0, uint32_t b1, uint32_t b2,
-                              uint32_t* verts[3], uint64_t counts[3], uint64_t** heavy,
+cudaError_t build_lgs_classes(gpm_graph* G, uint32_t kmin, const uint32_t* bounds, int nclass,
+                              uint32_t** verts, uint64_t* counts, uint64_t** heavy,
                               uint64_t* heavy_count, cudaStream_t s) {
   const uint32_t n = G->g.n;
   uint32_t* flag = nullptr;
@@ -410,11 +410,10 @@ cudaError_t build_lgs_classes(gpm_graph* G, uint32_t kmin, uint32_t b0, uint32_t
   cudaError_t e = cudaMalloc((void**)&flag, ((size_t)n + 1) * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc((void**)&pos, ((size_t)n + 1) * sizeof(int64_t));
   const unsigned blocks = std::max(1u, std::min<unsigned>((n + 255) / 256, G->num_sms * 8u));
-  const uint32_t bounds[4] = {0, b0, b1, b2};
-  for (int c = 0; c < 3 && e == cudaSuccess; c++) {
+  for (int c = 0; c < nclass && e == cudaSuccess; c++) {
     verts[c] = nullptr;
     counts[c] = 0;
-    k_lgs_flags<<<blocks, 256, 0, s>>>(G->doff_d, n, kmin, bounds[c], bounds[c + 1], flag);
+    k_lgs_flags<<<blocks, 256, 0, s>>>(G->doff_d, n, kmin, c ? bounds[c - 1] : 0u, bounds[c], flag);
     e = exclusive_scan(flag, n, pos, s);
     int64_t total = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&total, pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
@@ -426,7 +425,7 @@ cudaError_t build_lgs_classes(gpm_graph* G, uint32_t kmin, uint32_t b0, uint32_t
   *heavy = nullptr;
   *heavy_count = 0;
   if (e == cudaSuccess && n) {
-    k_heavy_deg<<<blocks, 256, 0, s>>>(G->doff_d, n, b2, flag);
+    k_heavy_deg<<<blocks, 256, 0, s>>>(G->doff_d, n, bounds[nclass - 1], flag);
     e = exclusive_scan(flag, n, pos, s);
     int64_t total = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&total, pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
