@@ -199,6 +199,160 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _batch_graph(i):
+    import graphgen as gg
+    g = gg.batch_graph(i)
+    return g.n, g.offsets, g.nbrs
+
+
+def run_batch(args):
+    """Batched induced k-motif counting over the seeded batch graphs (graph i
+    seeded 4000+i), one persistent launch per kernel family over all graphs,
+    against the plain path: the same kernels one graph per launch sequence."""
+    import multiprocessing as mp
+    nb = args.batch_graphs
+    t0 = time.time()
+    with mp.get_context("spawn").Pool(min(nb, os.cpu_count() or 1)) as pool:
+        raw = pool.map(_batch_graph, range(nb))
+    gen_s = time.time() - t0
+    import torch
+    import paper_2112_09761_gb300 as G
+    torch.cuda.set_device(0)
+    G.build()
+    edges = sum(int(off[-1]) // 2 for _, off, _ in raw)
+    hs = [G.gpm_load_csr(off, nbr, n) for n, off, nbr in raw]
+    k = args.motif_k
+    tc = time.time()
+    b = G.gpm_batch_create(hs, k)
+    create_s = time.time() - tc
+    info = G.gpm_batch_info(b)
+    ref = G.gpm_batch_count(b)
+    singles = []
+    for h in hs:
+        sb = G.gpm_batch_create([h], k, {"chunk": info["chunk"], "bsearch_ratio": info["bsearch_ratio"],
+                                         "warps_per_block": info["warps_per_block"]})
+        singles.append(sb)
+    for i, sb in enumerate(singles):
+        assert np.array_equal(G.gpm_batch_count(sb)[0], ref[i])
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        z = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        z.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(z) / 1e3 / steps
+
+    batched_s = timed(lambda: G.gpm_batch_count(b), args.steps)
+    plain_s = timed(lambda: [G.gpm_batch_count(sb) for sb in singles], max(1, args.steps // 2))
+    line = {"metric": "edges/s", "value": edges / batched_s, "unit": "edges/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": batched_s * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": f"batch-{nb}", "graphs": nb, "edges": edges,
+                       "motifs": f"induced {k}-motifs", "graph": "graph i: seed 4000+i, n ~ U{1K..200K}, "
+                       "avg degree ~ U[4,64], even i G(n,m), odd i R-MAT a=0.57",
+                       "autotuned": info},
+            "batched": {"s_per_step": batched_s, "graphs_per_s": nb / batched_s,
+                        "edges_per_s": edges / batched_s},
+            "plain": {"s_per_step": plain_s, "graphs_per_s": nb / plain_s,
+                      "edges_per_s": edges / plain_s},
+            "batched_over_plain": plain_s / batched_s, "gen_s": gen_s, "create_s": create_s}
+    print(json.dumps(line), flush=True)
+    for sb in singles:
+        G.gpm_batch_free(sb)
+    G.gpm_batch_free(b)
+    for h in hs:
+        G.gpm_graph_free(h)
+
+
+def run_serve(args):
+    """Serving: Poisson arrivals of (graph, pattern) count queries against
+    resident graphs at load rho x mu (mu = the plain path's closed-loop rate on
+    the same mix), through the library's server, against the plain path (one
+    query at a time, arrival order) at the same arrivals."""
+    import threading
+    import torch
+    import graphgen as gg
+    import paper_2112_09761_gb300 as G
+    torch.cuda.set_device(0)
+    G.build()
+    names = args.serve_graphs.split(",")
+    graphs = {nm: G.Graph.from_csr(gg.workload(nm)) for nm in names}
+    pats = ["triangle", "4-clique", "5-clique", "4-cycle", "diamond", "tailed-triangle"]
+    mix = [(nm, p) for nm in names for p in pats]
+    alone, service = {}, {}
+    for nm, p in mix:  # plan + warm-up, then the plain service time
+        graphs[nm].count(p)
+        torch.cuda.synchronize()
+        t = time.time()
+        alone[(nm, p)] = graphs[nm].count(p)
+        service[(nm, p)] = time.time() - t
+    mu = len(mix) / sum(service.values())
+    rng = np.random.default_rng(55)
+    results = {}
+    for rho in (0.5, 0.8, 0.95):
+        lam = rho * mu
+        q = args.serve_queries
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, q))
+        picks = rng.integers(0, len(mix), q)
+        # plain: FIFO, one query at a time
+        lat_plain = []
+        t0 = time.time()
+        busy_until = 0.0
+        for a, i in zip(arrivals, picks):
+            now = time.time() - t0
+            if now < a:
+                time.sleep(a - now)
+            nm, p = mix[i]
+            c = graphs[nm].count(p)
+            assert c == alone[(nm, p)]
+            lat_plain.append(time.time() - t0 - a)
+        plain_wall = time.time() - t0
+        # served: submit at the arrival times, collect all
+        srv = G.gpm_server_create(64 << 30, args.serve_inflight)
+        for nm, p in mix:  # build the server's plans before the clock starts
+            G.gpm_server_wait(srv, G.gpm_server_submit(srv, graphs[nm].handle, p))
+        tickets = []
+        t0 = time.time()
+        for a, i in zip(arrivals, picks):
+            now = time.time() - t0
+            if now < a:
+                time.sleep(a - now)
+            nm, p = mix[i]
+            tickets.append((G.gpm_server_submit(srv, graphs[nm].handle, p), (nm, p)))
+        lat_srv = []
+        for t, key in tickets:
+            c, l = G.gpm_server_wait(srv, t, 600.0)
+            assert c == alone[key], key
+            lat_srv.append(l)
+        srv_wall = time.time() - t0
+        st = G.gpm_server_stats(srv)
+        G.gpm_server_free(srv)
+        results[str(rho)] = {
+            "offered_qps": lam,
+            "served": {"p50_s": float(np.percentile(lat_srv, 50)), "p99_s": float(np.percentile(lat_srv, 99)),
+                       "qps": q / srv_wall, "peak_inflight": st["peak_inflight"]},
+            "plain": {"p50_s": float(np.percentile(lat_plain, 50)), "p99_s": float(np.percentile(lat_plain, 99)),
+                      "qps": q / plain_wall}}
+    line = {"metric": "queries/s", "value": results["0.95"]["served"]["qps"], "unit": "queries/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "serve", "graphs": names, "patterns": pats,
+                       "queries_per_rho": args.serve_queries, "inflight": args.serve_inflight,
+                       "arrivals": "Poisson, seed 55"},
+            "plain_mu_qps": mu, "service_s": {f"{nm}/{p}": service[(nm, p)] for nm, p in mix},
+            "by_rho": results}
+    print(json.dumps(line), flush=True)
+    for h in graphs.values():
+        h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -209,12 +363,24 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--mode", default="count", choices=["count", "batch", "serve"])
+    ap.add_argument("--batch-graphs", type=int, default=200)
+    ap.add_argument("--motif-k", type=int, default=4)
+    ap.add_argument("--serve-queries", type=int, default=100)
+    ap.add_argument("--serve-graphs", default="er-10k,rmat22,chunglu-1m")
+    ap.add_argument("--serve-inflight", type=int, default=8)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.mode == "batch":
+        run_batch(args)
+        return
+    if args.mode == "serve":
+        run_serve(args)
         return
 
     import torch
