@@ -146,9 +146,11 @@ __global__ void __launch_bounds__(256) k_lgs_warp(LgsArgs a) {
 //
 // f_L(S) = number of L-cliques of the local DAG inside candidate set S:
 //   f_1(S) = |S|,  f_L(S) = sum over x in S of f_{L-1}(S ∩ row_x).
-// A set with at most 64 members is first compressed to its own 64x64 bitmap
-// (one uint64 row per member, in shared memory) and finished lane-parallel,
-// one lane per member; larger sets iterate their members warp-cooperatively.
+// Above the last two levels, a set with at most 64 members is first
+// compressed to its own 64x64 bitmap (one uint64 row per member, in shared
+// memory) and finished lane-parallel, one lane per member; larger sets iterate
+// their members warp-cooperatively.  The last two levels (edges inside a set)
+// always run lane-parallel over members, word by word.
 
 // CTA shape per class: NW words per row (members <= 32*NW); 512 threads for
 // the 8- and 16-word classes (several CTAs per SM), 1024 for the 32-word class
@@ -254,7 +256,10 @@ __device__ __forceinline__ unsigned long long f_set(uint32_t S, const uint32_t* 
     const uint32_t lane = lane_id();
     const uint32_t s = __reduce_add_sync(kFull, __popc(S));
     if (s < (uint32_t)L) return 0;
-    if (s <= 64) {
+    // compress small sets only where deeper levels reuse the compressed rows
+    // (L >= 3); for the last two vertices (L = 2) each row is read once, and
+    // the word loop below is cheaper than building the compressed rows
+    if (L >= 3 && s <= 64) {
       compact_set(S, ws.list);
       return f_small<L, NW, ST>(s, rows, ws, wop);
     }
