@@ -246,6 +246,39 @@ __device__ __forceinline__ unsigned long long f_small(uint32_t s, const uint32_t
   return t;
 }
 
+// f_3(S), the triangles inside S, lane-parallel over the members x of S:
+// each lane walks the members y of S ∩ row_x and adds |S ∩ row_x ∩ row_y|
+// word by word.  S is compacted once; the sets S ∩ row_x are never
+// materialised (rows are triangular, so words start after x and after y).
+template <int NW, bool ST>
+__device__ __forceinline__ unsigned long long f3_lanes(uint32_t S, uint32_t s, const uint32_t* rows,
+                                                       uint32_t nw, const WarpScratch& ws,
+                                                       unsigned long long& wop) {
+  constexpr int STRIDE = NW + 1;
+  const uint32_t lane = lane_id();
+  compact_set(S, ws.list);
+  ws.sb[lane] = S;
+  __syncwarp();
+  unsigned long long acc = 0;
+  for (uint32_t k = lane; k < s; k += 32) {
+    const uint32_t x = ws.list[k];
+    const uint32_t* rx = rows + x * STRIDE;
+    for (uint32_t w = (x + 1) >> 5; w < nw; w++) {
+      uint32_t t = ws.sb[w] & rx[w];
+      if constexpr (ST) wop += 1;
+      while (t) {
+        const uint32_t y = w * 32 + __ffs(t) - 1;
+        t &= t - 1;
+        const uint32_t* ry = rows + y * STRIDE;
+        for (uint32_t w2 = (y + 1) >> 5; w2 < nw; w2++) acc += __popc(ws.sb[w2] & rx[w2] & ry[w2]);
+        if constexpr (ST) wop += nw - ((y + 1) >> 5);
+      }
+    }
+  }
+  __syncwarp();
+  return acc;
+}
+
 template <int L, int NW, bool ST>
 __device__ __forceinline__ unsigned long long f_set(uint32_t S, const uint32_t* rows, uint32_t nw,
                                                     const WarpScratch& ws, unsigned long long& wop) {
@@ -263,6 +296,7 @@ __device__ __forceinline__ unsigned long long f_set(uint32_t S, const uint32_t* 
       compact_set(S, ws.list);
       return f_small<L, NW, ST>(s, rows, ws, wop);
     }
+    if constexpr (L == 3) return f3_lanes<NW, ST>(S, s, rows, nw, ws, wop);
     if constexpr (L == 2) {
       // edges inside S: lanes take members x, |S ∩ row_x| word by word
       compact_set(S, ws.list);
