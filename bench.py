@@ -111,6 +111,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def measured_traffic(workload, pattern):
+    """DRAM bytes of one count from a committed ncu summary, if the library's
+    sources still match the digest the counters were taken with."""
+    import re
+    from paper_2112_09761_gb300 import _build
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}_{pattern.replace('-', '')}.md")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        text = f.read()
+    dig = re.search(r"^digest: (\w+)$", text, re.M)
+    val = re.search(r"^dram_bytes_per_count: (\d+)$", text, re.M)
+    if not dig or not val or dig.group(1) != _build._digest():
+        return None
+    return int(val.group(1))
+
+
 def roofline_for(pattern, st, seconds, props):
     """Roofline object of the kernel(s) of one gpm_count of `pattern`.
 
@@ -452,6 +469,7 @@ def main():
     st = G.gpm_plan_stats(sp)
     G.gpm_plan_free(sp)
     roofline = roofline_for(dom, st, per_pat_s[dom], torch.cuda.get_device_properties(local))
+    roofline["traffic"] = measured_traffic(args.workload, dom)
 
     # ---- end to end through the public API from pinned host memory
     off_h = torch.from_numpy(g.offsets).pin_memory()
