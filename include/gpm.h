@@ -128,7 +128,8 @@ typedef struct gpm_plan_opts {
   uint32_t bsearch_ratio;    /* |B| >= ratio * |A| selects binary search over merge */
   uint32_t no_count_only;    /* 1 = enumerate even where a counting-only form exists */
   uint32_t collect_stats;    /* 1 = count algorithmic bytes / set operations (slower) */
-  uint32_t no_lgs;           /* 1 = cliques without local graph search (sorted sets only) */
+  uint32_t no_lgs;           /* 1 = cliques (and batched 4-cliques) without local graph
+                                search (sorted sets only) */
   uint32_t reserved[1];
 } gpm_plan_opts;
 
@@ -217,8 +218,11 @@ typedef struct gpm_batch_s gpm_batch_t;
  * Builds each graph's DAG and task lists if not cached.  With opts->chunk,
  * opts->bsearch_ratio and opts->warps_per_block all zero, an autotuner times
  * candidate task-chunk sizes, intersection thresholds and CTA shapes on the
- * batch itself and keeps the fastest; nonzero fields fix them.  The graphs
- * must outlive the batch.  Returns GPM_E_INVALID_ARG for k not in {3, 4} or
+ * batch itself and keeps the fastest; nonzero fields fix them.  For k = 4 the
+ * 4-cliques of all graphs are counted by local graph search (bitmap local
+ * graphs, roots of every graph sorted into out-degree classes once here)
+ * unless opts->no_lgs is set, in which case the sorted-set kernel counts
+ * them; both give the same counts.  The graphs must outlive the batch.  Returns GPM_E_INVALID_ARG for k not in {3, 4} or
  * n_graphs = 0.
  */
 gpm_status gpm_batch_create(gpm_graph* const* graphs, uint32_t n_graphs, uint32_t k,

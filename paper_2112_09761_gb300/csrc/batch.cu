@@ -17,6 +17,12 @@ namespace gpm {
 
 cudaError_t degrees32(const DevCsr& g, uint32_t* deg, int sms, cudaStream_t s);
 void set_error(const std::string& msg);
+uint32_t lgs_warp_max_degree();
+uint32_t lgs_block_max_degree();
+cudaError_t lgs_launch_warp(int k, const LgsArgs& a, unsigned blocks, cudaStream_t s);
+cudaError_t lgs_launch_block(int k, int nw, bool arc, const LgsArgs& a, unsigned blocks_per_sm,
+                             unsigned sms, cudaStream_t s);
+int lgs_block_occupancy(int k, int nw);
 
 }  // namespace gpm
 
@@ -30,12 +36,21 @@ struct gpm_batch_s {
   uint64_t* prefix_d[3] = {nullptr, nullptr, nullptr};  // edge tasks, arcs, vertices
   uint64_t totals[3] = {0, 0, 0};
   unsigned long long* sums_d = nullptr;   // [n_graphs][kNumSums]
-  unsigned long long* next_d = nullptr;   // 4 queue heads
+  unsigned long long* next_d = nullptr;   // kQueues queue heads and counters
   unsigned long long* sums_h = nullptr;   // pinned
   uint32_t* c4_cnt = nullptr;
   uint32_t max_n = 0;
   unsigned c4_blocks = 0;
   uint32_t k4_scap = 0;
+  // 4-cliques by local graph search (unless disabled): root lists of the
+  // whole batch, per-graph descriptors, heavy arcs whose arc-level local graph
+  // is too large (counted by k_motif_k4 from their list)
+  bool lgs = false;
+  BatchRoots roots;
+  LgsGraph* lgs_graphs_d = nullptr;
+  uint64_t* overflow_d = nullptr;
+  unsigned lgs_warp_blocks = 1;
+  unsigned lgs_bps[4] = {1, 1, 1, 1};
   uint32_t chunk = 16, ratio = 8, wpb = 8;
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
@@ -43,6 +58,12 @@ struct gpm_batch_s {
 };
 
 namespace {
+
+// next_d slots: queue heads of the edge, vertex, k4 and c4 kernels, of the
+// four LGS classes and the heavy arcs, of the overflow pass, and the overflow
+// list length
+constexpr int kQueues = 11;
+constexpr int kQLgs = 4, kQHeavy = 8, kQOverflow = 9, kOverflowCount = 10;
 
 gpm_status fail(gpm_status st, const std::string& m) {
   set_error(m);
@@ -62,20 +83,61 @@ MotifBatchArgs args_for(const gpm_batch_s* b, int space, int queue) {
   a.sums = b->sums_d;
   a.chunk = b->chunk;
   a.ratio = b->ratio;
+  a.idx = nullptr;
+  a.idx_count = nullptr;
   return a;
+}
+
+// 4-cliques of the whole batch by local graph search: one launch per
+// out-degree class, one over the arcs of heavier roots, then the sorted-set
+// kernel over the arcs whose arc-level local graph is still too large.
+cudaError_t enqueue_lgs_k4(gpm_batch_s* b, cudaStream_t s) {
+  static const int kClassWords[4] = {0, 8, 16, 32};
+  const unsigned sms = (unsigned)b->num_sms;
+  LgsArgs la{};
+  la.lo = 0;
+  la.hi = ~0ull;
+  la.graphs = b->lgs_graphs_d;
+  la.gsums = b->sums_d;
+  la.gstride = kNumSums;
+  la.gslot = kK4;
+  la.overflow = b->overflow_d;
+  la.overflow_count = b->next_d + kOverflowCount;
+  cudaError_t e = cudaSuccess;
+  for (int c = 0; c < 4 && e == cudaSuccess; c++) {
+    if (!b->roots.count[c]) continue;
+    la.broots = b->roots.roots[c];
+    la.nverts = b->roots.count[c];
+    la.next = b->next_d + kQLgs + c;
+    if (c == 0) e = lgs_launch_warp(4, la, b->lgs_warp_blocks, s);
+    else e = lgs_launch_block(4, kClassWords[c], false, la, b->lgs_bps[c], sms, s);
+  }
+  if (e == cudaSuccess && b->roots.heavy_count) {
+    la.broots = b->roots.heavy;
+    la.nverts = 0;
+    la.nidx = b->roots.heavy_count;
+    la.next = b->next_d + kQHeavy;
+    e = lgs_launch_block(4, 32, true, la, b->lgs_bps[3], sms, s);
+    MotifBatchArgs m = args_for(b, 1, kQOverflow);
+    m.idx = b->overflow_d;
+    m.idx_count = b->next_d + kOverflowCount;
+    if (e == cudaSuccess) e = launch_motif_k4(m, sms * (64 / b->wpb), b->wpb * 32, b->k4_scap, s);
+  }
+  return e;
 }
 
 // Enqueue one full batch evaluation on stream s (also used under capture).
 cudaError_t enqueue(gpm_batch_s* b, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(b->sums_d, 0, (size_t)b->n_graphs * kNumSums * sizeof(unsigned long long), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->next_d, 0, 4 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->next_d, 0, kQueues * sizeof(unsigned long long), s);
   const unsigned sms = (unsigned)b->num_sms;
   if (e == cudaSuccess && b->totals[0])
     e = launch_motif_edges(args_for(b, 0, 0), sms * (64 / b->wpb), b->wpb * 32, s);
   if (e == cudaSuccess && b->totals[2])
     e = launch_motif_vertices(args_for(b, 2, 1), sms * 4, s);
   if (b->k == 4) {
-    if (e == cudaSuccess && b->totals[1])
+    if (e == cudaSuccess && b->lgs) e = enqueue_lgs_k4(b, s);
+    else if (e == cudaSuccess && b->totals[1])
       e = launch_motif_k4(args_for(b, 1, 2), sms * (64 / b->wpb), b->wpb * 32, b->k4_scap, s);
     if (e == cudaSuccess && b->totals[2])
       e = launch_motif_c4(args_for(b, 2, 3), b->c4_blocks, b->c4_cnt, b->max_n, s);
@@ -148,6 +210,7 @@ gpm_status gpm_batch_create(gpm_graph* const* graphs, uint32_t n_graphs, uint32_
   std::vector<uint64_t> pre[3];
   for (auto& v : pre) v.assign(n_graphs + 1, 0);
   uint32_t max_dplus = 1;
+  uint64_t max_arcs = 0;
   cudaError_t e = cudaSuccess;
   for (uint32_t i = 0; i < n_graphs && e == cudaSuccess; i++) {
     gpm_graph* G = graphs[i];
@@ -169,6 +232,7 @@ gpm_status gpm_batch_create(gpm_graph* const* graphs, uint32_t n_graphs, uint32_
     pre[2][i + 1] = pre[2][i] + G->g.n;
     b->max_n = std::max(b->max_n, G->g.n);
     max_dplus = std::max(max_dplus, G->max_out_degree);
+    max_arcs = std::max<uint64_t>(max_arcs, G->dag_arcs);
   }
   if (e != cudaSuccess) { gpm_batch_free(b); return cfail(e, "gpm_batch_create preprocessing"); }
   for (int sp = 0; sp < 3; sp++) b->totals[sp] = pre[sp][n_graphs];
@@ -179,7 +243,7 @@ gpm_status gpm_batch_create(gpm_graph* const* graphs, uint32_t n_graphs, uint32_
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->prefix_d[sp], pre[sp].data(), (n_graphs + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, s);
   }
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->sums_d, (size_t)n_graphs * kNumSums * sizeof(unsigned long long));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->next_d, 4 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->next_d, kQueues * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->sums_h, (size_t)n_graphs * kNumSums * sizeof(unsigned long long));
   if (e == cudaSuccess && k == 4) {
     b->k4_scap = std::min<uint32_t>(max_dplus, 512);
@@ -192,13 +256,35 @@ gpm_status gpm_batch_create(gpm_graph* const* graphs, uint32_t n_graphs, uint32_
     e = cudaMalloc((void**)&b->c4_cnt, blocks * per);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->c4_cnt, 0, blocks * per, s);
   }
+  gpm_plan_opts o;
+  memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  // packed roots hold the graph index in the top 24 bits of an arc root
+  const bool packable = n_graphs < (1u << 24) && max_arcs < (1ull << 40);
+  if (e == cudaSuccess && k == 4 && !o.no_lgs && b->totals[1] && packable) {
+    // vertex roots by out-degree class, the arcs of heavier roots, and the
+    // descriptors the LGS kernels read their graph from
+    b->lgs = true;
+    const uint32_t bounds[4] = {lgs_warp_max_degree(), 256, 512, lgs_block_max_degree()};
+    MotifBatchArgs va = args_for(b, 2, 0);
+    e = build_batch_roots(va, b->totals[2], 3, bounds, 4, b->num_sms, &b->roots, s);
+    std::vector<LgsGraph> lg(n_graphs);
+    for (uint32_t i = 0; i < n_graphs; i++) lg[i] = LgsGraph{hg[i].dag, hg[i].g.off, hg[i].dsrc};
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->lgs_graphs_d, n_graphs * sizeof(LgsGraph));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->lgs_graphs_d, lg.data(), n_graphs * sizeof(LgsGraph), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && b->roots.heavy_count)
+      e = cudaMalloc((void**)&b->overflow_d, b->roots.heavy_count * sizeof(uint64_t));
+    b->lgs_warp_blocks = (unsigned)std::min<uint64_t>(
+        (uint64_t)b->num_sms * 8, std::max<uint64_t>(1, (b->roots.count[0] + 7) / 8));
+    b->lgs_bps[1] = (unsigned)lgs_block_occupancy(4, 8);
+    b->lgs_bps[2] = (unsigned)lgs_block_occupancy(4, 16);
+    b->lgs_bps[3] = (unsigned)lgs_block_occupancy(4, 32);
+  }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) { gpm_batch_free(b); return cfail(e, "gpm_batch_create"); }
 
-  gpm_plan_opts o;
-  memset(&o, 0, sizeof(o));
-  if (opts) o = *opts;
   if (o.chunk || o.bsearch_ratio || o.warps_per_block) {
     b->chunk = o.chunk ? o.chunk : 16;
     b->ratio = o.bsearch_ratio ? o.bsearch_ratio : 8;
@@ -263,6 +349,9 @@ void gpm_batch_free(gpm_batch_t* b) {
   cudaFree(b->next_d);
   if (b->sums_h) cudaFreeHost(b->sums_h);
   cudaFree(b->c4_cnt);
+  free_batch_roots(&b->roots);
+  cudaFree(b->lgs_graphs_d);
+  cudaFree(b->overflow_d);
   delete b;
 }
 

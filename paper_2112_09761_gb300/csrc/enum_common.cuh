@@ -37,6 +37,13 @@ struct EnumArgs {
   const unsigned long long* idx_count;  // null, or the device-side length of idx
 };
 
+// One graph of a batch as the local-graph-search kernels see it.
+struct LgsGraph {
+  DevCsr dag;            // degree-oriented DAG
+  const int64_t* uoff;   // undirected offsets (degrees)
+  const uint32_t* src;   // DAG arc sources
+};
+
 // Arguments of the local-graph-search clique kernels (enum_lgs.cu).
 struct LgsArgs {
   DevCsr dag;
@@ -54,6 +61,14 @@ struct LgsArgs {
   const uint32_t* src;
   uint64_t* overflow;
   unsigned long long* overflow_count;
+  // batch mode (graphs != null): roots are broots[0, nverts or nidx) packed as
+  // graph << 32 | vertex (vertex roots) or graph << 40 | arc (arc roots); each
+  // root's count is added to gsums[graph * gstride + gslot]; overflow arcs are
+  // appended packed the same way
+  const LgsGraph* graphs;
+  const uint64_t* broots;
+  unsigned long long* gsums;
+  uint32_t gstride, gslot;
 };
 
 // Algorithmic bytes of one set operation A∘B (|A| <= |B| after ordering):

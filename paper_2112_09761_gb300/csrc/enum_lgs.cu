@@ -78,7 +78,7 @@ __device__ __forceinline__ unsigned long long count64(const unsigned long long* 
   }
 }
 
-template <int K, bool ST>
+template <int K, bool ST, bool BATCH>
 __global__ void __launch_bounds__(256) k_lgs_warp(LgsArgs a) {
   __shared__ unsigned long long s_rows[8][kWarpMaxD];
   __shared__ unsigned long long s_acc;
@@ -94,21 +94,35 @@ __global__ void __launch_bounds__(256) k_lgs_warp(LgsArgs a) {
     if (start >= a.nverts) break;
     const uint64_t end = min((uint64_t)start + 4, a.nverts);
     for (uint64_t q = start; q < end; q++) {
-      const uint32_t u = a.verts[q];
-      const int64_t o0 = a.dag.off[u], o1 = a.dag.off[u + 1];
+      DevCsr dag = a.dag;
+      uint32_t u;
+      uint64_t lo = a.lo, hi = a.hi;
+      unsigned long long* gout = nullptr;
+      if constexpr (BATCH) {
+        const uint64_t r = a.broots[q];
+        const LgsGraph& G = a.graphs[r >> 32];
+        dag = G.dag;
+        u = (uint32_t)r;
+        lo = 0;
+        hi = ~0ull;
+        gout = a.gsums + (r >> 32) * a.gstride + a.gslot;
+      } else {
+        u = a.verts[q];
+      }
+      const int64_t o0 = dag.off[u], o1 = dag.off[u + 1];
       const uint32_t d = (uint32_t)(o1 - o0);
-      const int64_t ia = max(o0, (int64_t)a.lo) - o0, ib = min(o1, (int64_t)a.hi) - o0;
+      const int64_t ia = max(o0, (int64_t)lo) - o0, ib = min(o1, (int64_t)min(hi, (uint64_t)o1)) - o0;
       if (ia >= ib) continue;
-      const uint32_t* A = a.dag.nbr + o0;
+      const uint32_t* A = dag.nbr + o0;
       const uint32_t a0 = (lane < d) ? A[lane] : kNone;
       const uint32_t a1 = (lane + 32 < d) ? A[lane + 32] : kNone;
       // local graph rows (only rows reachable from the root arcs in range are
       // needed; for a full range that is all of them)
       for (uint32_t i = (K == 3 ? (uint32_t)ia : 0); i < (K == 3 ? (uint32_t)ib : d); i++) {
         const uint32_t v = (i < 32) ? __shfl_sync(kFull, a0, i) : __shfl_sync(kFull, a1, i - 32);
-        const int64_t vs = a.dag.off[v];
-        const uint32_t dl = (uint32_t)(a.dag.off[v + 1] - vs);
-        const unsigned long long bits = row_bits64(a.dag.nbr + vs, dl, a0, a1, d);
+        const int64_t vs = dag.off[v];
+        const uint32_t dl = (uint32_t)(dag.off[v + 1] - vs);
+        const unsigned long long bits = row_bits64(dag.nbr + vs, dl, a0, a1, d);
         if (lane == 0) rows[i] = bits;
         if (a.stats) {
           const uint32_t lo2 = min(d, dl), hi2 = max(d, dl);
@@ -117,8 +131,15 @@ __global__ void __launch_bounds__(256) k_lgs_warp(LgsArgs a) {
         }
       }
       __syncwarp();
+      unsigned long long root = 0;
       for (uint32_t i = (uint32_t)ia + lane; i < (uint32_t)ib; i += 32)
-        acc += count64<K - 3, ST>(rows, rows[i], wop);
+        root += count64<K - 3, ST>(rows, rows[i], wop);
+      if constexpr (BATCH) {
+        root = warp_sum_u64(root);
+        if (lane == 0 && root) atomicAdd(gout, root);
+      } else {
+        acc += root;
+      }
       __syncwarp();
     }
   }
@@ -130,7 +151,7 @@ __global__ void __launch_bounds__(256) k_lgs_warp(LgsArgs a) {
     if (lane == 0 && wop) atomicAdd(&a.stats[2], wop);
   }
   __syncthreads();
-  if (threadIdx.x == 0 && s_acc) atomicAdd(a.result, s_acc);
+  if (!BATCH && threadIdx.x == 0 && s_acc) atomicAdd(a.result, s_acc);
 }
 
 // ---------------------------------------------------------------- CTA class
@@ -333,7 +354,7 @@ __device__ __forceinline__ unsigned long long f_set(uint32_t S, const uint32_t* 
 // ARC = false: roots are vertices u of a.verts; ARC = true: roots are the
 // arcs a.idx[q] (members N+(u) ∩ N+(v)); roots whose member set exceeds
 // 32*NW are appended to a.overflow for the sorted-set kernel.
-template <int K, int NW, bool ARC, bool ST>
+template <int K, int NW, bool ARC, bool ST, bool BATCH>
 __global__ void __launch_bounds__(BlockShape<NW>::THREADS) k_lgs_block(LgsArgs a) {
   using SM = BlockSmem<NW>;
   constexpr int kWarps = BlockShape<NW>::WARPS;
@@ -364,28 +385,48 @@ __global__ void __launch_bounds__(BlockShape<NW>::THREADS) k_lgs_block(LgsArgs a
     __syncthreads();
     const uint64_t q = s_q;
     if (q >= nroots) break;
+    // the root's graph: the plan's, or (batch) the one packed into the root
+    DevCsr dag = a.dag;
+    const int64_t* uoff = a.uoff;
+    const uint32_t* src = a.src;
+    uint64_t lo = a.lo, hi = a.hi, rootv = 0;
+    unsigned long long* gout = nullptr;
+    if constexpr (BATCH) {
+      const uint64_t r = a.broots[q];
+      const uint64_t g = ARC ? (r >> 40) : (r >> 32);
+      const LgsGraph& G = a.graphs[g];
+      dag = G.dag;
+      uoff = G.uoff;
+      src = G.src;
+      lo = 0;
+      hi = ~0ull;
+      rootv = ARC ? (r & ((1ull << 40) - 1)) : (r & 0xffffffffull);
+      gout = a.gsums + g * a.gstride + a.gslot;
+    } else {
+      rootv = ARC ? a.idx[q] : a.verts[q];
+    }
     uint32_t d = 0;
     int64_t ia = 0, ib = 0;  // root arcs (member positions, id order) to count
     if constexpr (!ARC) {
-      const uint32_t u = a.verts[q];
-      const int64_t o0 = a.dag.off[u], o1 = a.dag.off[u + 1];
+      const uint32_t u = (uint32_t)rootv;
+      const int64_t o0 = dag.off[u], o1 = dag.off[u + 1];
       d = (uint32_t)(o1 - o0);
-      ia = max(o0, (int64_t)a.lo) - o0;
-      ib = min(o1, (int64_t)a.hi) - o0;
+      ia = max(o0, (int64_t)lo) - o0;
+      ib = min(o1, (int64_t)min(hi, (uint64_t)o1)) - o0;
       if (ia >= ib || d > (uint32_t)MAXD) continue;  // block-uniform
-      for (uint32_t t = threadIdx.x; t < d; t += blockDim.x) aid[t] = a.dag.nbr[o0 + t];
+      for (uint32_t t = threadIdx.x; t < d; t += blockDim.x) aid[t] = dag.nbr[o0 + t];
     } else {
-      const uint64_t e = a.idx[q];
-      if (e < a.lo || e >= a.hi) continue;
-      const uint32_t u = a.src[e], v = a.dag.nbr[e];
-      const int64_t u0 = a.dag.off[u], v0 = a.dag.off[v];
-      const uint32_t du = (uint32_t)(a.dag.off[u + 1] - u0), dv = (uint32_t)(a.dag.off[v + 1] - v0);
+      const uint64_t e = rootv;
+      if (e < lo || e >= hi) continue;
+      const uint32_t u = src[e], v = dag.nbr[e];
+      const int64_t u0 = dag.off[u], v0 = dag.off[v];
+      const uint32_t du = (uint32_t)(dag.off[u + 1] - u0), dv = (uint32_t)(dag.off[v + 1] - v0);
       if (min(du, dv) > (uint32_t)MAXD) {
-        if (threadIdx.x == 0) a.overflow[atomicAdd(a.overflow_count, 1ull)] = e;
+        if (threadIdx.x == 0) a.overflow[atomicAdd(a.overflow_count, 1ull)] = BATCH ? a.broots[q] : e;
         continue;
       }
       if (wib == 0) {
-        const uint32_t c = warp_intersect<kWrite>(a.dag.nbr + u0, du, a.dag.nbr + v0, dv, aid, 8);
+        const uint32_t c = warp_intersect<kWrite>(dag.nbr + u0, du, dag.nbr + v0, dv, aid, 8);
         if (lane == 0) s_d = c;
       }
       __syncthreads();
@@ -398,7 +439,7 @@ __global__ void __launch_bounds__(BlockShape<NW>::THREADS) k_lgs_block(LgsArgs a
     for (uint32_t t = threadIdx.x; t < P; t += blockDim.x) {
       if (t < d) {
         const uint32_t v = aid[t];
-        key[t] = ((unsigned long long)(a.uoff[v + 1] - a.uoff[v]) << 32) | v;  // orientation key
+        key[t] = ((unsigned long long)(uoff[v + 1] - uoff[v]) << 32) | v;  // orientation key
       } else {
         key[t] = ~0ull;
       }
@@ -430,9 +471,9 @@ __global__ void __launch_bounds__(BlockShape<NW>::THREADS) k_lgs_block(LgsArgs a
     // rows in rank order: one warp per member
     for (uint32_t i = wib; i < d; i += kWarps) {
       const uint32_t v = aid[ridx[i]];
-      const int64_t vs = a.dag.off[v];
-      const uint32_t dl = (uint32_t)(a.dag.off[v + 1] - vs);
-      const uint32_t* Lv = a.dag.nbr + vs;
+      const int64_t vs = dag.off[v];
+      const uint32_t dl = (uint32_t)(dag.off[v + 1] - vs);
+      const uint32_t* Lv = dag.nbr + vs;
       if (dl == 0) continue;
       if (dl >= 2 * d) {
         const uint32_t piv = Lv[(uint32_t)(((uint64_t)lane * dl) >> 5)];
@@ -473,14 +514,21 @@ __global__ void __launch_bounds__(BlockShape<NW>::THREADS) k_lgs_block(LgsArgs a
       r = __shfl_sync(kFull, r, 0);
       if (r >= d) break;
       const uint32_t m = (lane < nw) ? rows[r * STRIDE + lane] : 0u;
+      unsigned long long c;
       if constexpr (!ARC) {
         // root arc (u, member r): K-cliques = (K-2)-cliques inside row_r
         const int64_t id_pos = ridx[r];
         if (id_pos < ia || id_pos >= ib) continue;
-        acc += f_set<K - 2, NW, ST>(m, rows, nw, ws, wop);
+        c = f_set<K - 2, NW, ST>(m, rows, nw, ws, wop);
       } else {
         // root arc (u, v), third vertex = member r: (K-3)-cliques inside row_r
-        acc += f_set<K - 3, NW, ST>(m, rows, nw, ws, wop);
+        c = f_set<K - 3, NW, ST>(m, rows, nw, ws, wop);
+      }
+      if constexpr (BATCH) {
+        c = warp_sum_u64(c);
+        if (lane == 0 && c) atomicAdd(gout, c);
+      } else {
+        acc += c;
       }
     }
   }
@@ -492,20 +540,33 @@ __global__ void __launch_bounds__(BlockShape<NW>::THREADS) k_lgs_block(LgsArgs a
     if (lane == 0 && wop) atomicAdd(&a.stats[2], wop);
   }
   __syncthreads();
-  if (threadIdx.x == 0 && s_acc) atomicAdd(a.result, s_acc);
+  if (!BATCH && threadIdx.x == 0 && s_acc) atomicAdd(a.result, s_acc);
 }
 
+// Batch roots (a.graphs set) are only instantiated for 4-cliques, the size
+// the batched motif counts need.
 template <int K>
 cudaError_t launch_warp_k(const LgsArgs& a, unsigned blocks, cudaStream_t s) {
-  if (a.stats) k_lgs_warp<K, true><<<blocks, 256, 0, s>>>(a);
-  else k_lgs_warp<K, false><<<blocks, 256, 0, s>>>(a);
+  if (a.graphs) {
+    if constexpr (K == 4) k_lgs_warp<K, false, true><<<blocks, 256, 0, s>>>(a);
+    else return cudaErrorInvalidValue;
+  } else if (a.stats) {
+    k_lgs_warp<K, true, false><<<blocks, 256, 0, s>>>(a);
+  } else {
+    k_lgs_warp<K, false, false><<<blocks, 256, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
 template <int K, int NW, bool ARC>
 cudaError_t launch_block_k(const LgsArgs& a, unsigned blocks, cudaStream_t s) {
   const size_t smem = BlockSmem<NW>::bytes;
-  auto kern = a.stats ? k_lgs_block<K, NW, ARC, true> : k_lgs_block<K, NW, ARC, false>;
+  void (*kern)(LgsArgs) = a.stats ? k_lgs_block<K, NW, ARC, true, false>
+                                  : k_lgs_block<K, NW, ARC, false, false>;
+  if (a.graphs) {
+    if constexpr (K == 4) kern = k_lgs_block<K, NW, ARC, false, true>;
+    else return cudaErrorInvalidValue;
+  }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<blocks, BlockShape<NW>::THREADS, smem, s>>>(a);
@@ -515,7 +576,7 @@ cudaError_t launch_block_k(const LgsArgs& a, unsigned blocks, cudaStream_t s) {
 template <int K, int NW>
 int occ_block_k() {
   const size_t smem = BlockSmem<NW>::bytes;
-  auto kern = k_lgs_block<K, NW, false, false>;
+  auto kern = k_lgs_block<K, NW, false, false, false>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 1;
   int b = 0;

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(256) k_motif_k4(MotifBatchArgs a, uint32_t sca
   extern __shared__ uint32_t s_w[];
   const uint32_t lane = lane_id();
   uint32_t* W = s_w + (threadIdx.x >> 5) * scap;
-  const uint64_t total = a.prefix[a.n_graphs];
+  const uint64_t total = a.idx ? (uint64_t)*a.idx_count : a.prefix[a.n_graphs];
   Partial<1> part;
   const int slots[1] = {kK4};
   uint32_t hint = 0;
@@ -147,14 +147,22 @@ __global__ void __launch_bounds__(256) k_motif_k4(MotifBatchArgs a, uint32_t sca
     if (start >= total) break;
     const uint64_t end = min((uint64_t)start + a.chunk, total);
     for (uint64_t t = start; t < end; t++) {
-      const uint32_t g = graph_of(a.prefix, a.n_graphs, t, hint);
-      hint = g;
+      uint32_t g;
+      uint64_t lt;
+      if (a.idx) {
+        const uint64_t r = a.idx[t];
+        g = (uint32_t)(r >> 40);
+        lt = r & ((1ull << 40) - 1);
+      } else {
+        g = graph_of(a.prefix, a.n_graphs, t, hint);
+        hint = g;
+        lt = t - a.prefix[g];
+      }
       if (g != part.g) {
         part.flush(a, slots);
         part.g = g;
       }
       const MotifGraph& G = a.graphs[g];
-      const uint64_t lt = t - a.prefix[g];
       const uint32_t u = G.dsrc[lt], v = G.dag.nbr[lt];
       const uint32_t du = (uint32_t)(G.dag.off[u + 1] - G.dag.off[u]);
       const uint32_t dv = (uint32_t)(G.dag.off[v + 1] - G.dag.off[v]);
@@ -258,6 +266,52 @@ __global__ void __launch_bounds__(kC4Threads) k_motif_c4(MotifBatchArgs a, uint3
   }
 }
 
+// Root lists of the batched local graph search.  mode 0: flag[t] = 1 if
+// vertex t of the batch (vertex space) has kmin <= d+, lo < d+ <= hi; mode 1:
+// flag[t] = d+ if d+ > lo (its arcs become arc roots), else 0.
+__global__ void k_broot_flags(MotifBatchArgs a, uint64_t total, uint32_t kmin, uint32_t lo,
+                              uint32_t hi, int mode, uint32_t* __restrict__ flag) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint32_t hint = 0;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+    const uint32_t g = graph_of(a.prefix, a.n_graphs, t, hint);
+    hint = g;
+    const DevCsr& dag = a.graphs[g].dag;
+    const uint64_t v = t - a.prefix[g];
+    const uint32_t d = (uint32_t)(dag.off[v + 1] - dag.off[v]);
+    if (mode == 0) flag[t] = (d >= kmin && d > lo && d <= hi) ? 1u : 0u;
+    else flag[t] = d > lo ? d : 0u;
+  }
+}
+
+__global__ void k_broot_scatter(MotifBatchArgs a, uint64_t total, const uint32_t* __restrict__ flag,
+                                const int64_t* __restrict__ pos, uint64_t* __restrict__ out) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint32_t hint = 0;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+    if (!flag[t]) continue;
+    const uint32_t g = graph_of(a.prefix, a.n_graphs, t, hint);
+    hint = g;
+    out[pos[t]] = ((uint64_t)g << 32) | (t - a.prefix[g]);
+  }
+}
+
+// warp per vertex: the arcs of a heavy vertex, packed graph << 40 | arc
+__global__ void k_broot_arcs(MotifBatchArgs a, uint64_t total, const uint32_t* __restrict__ cnt,
+                             const int64_t* __restrict__ pos, uint64_t* __restrict__ out) {
+  const uint32_t lane = lane_id();
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  uint32_t hint = 0;
+  for (uint64_t t = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < total; t += nwarps) {
+    const uint32_t c = cnt[t];
+    if (!c) continue;
+    const uint32_t g = graph_of(a.prefix, a.n_graphs, t, hint);
+    hint = g;
+    const uint64_t first = (uint64_t)a.graphs[g].dag.off[t - a.prefix[g]];
+    for (uint32_t i = lane; i < c; i += 32) out[pos[t] + i] = ((uint64_t)g << 40) | (first + i);
+  }
+}
+
 }  // namespace
 
 uint32_t motif_c4_threads() { return kC4Threads; }
@@ -286,6 +340,56 @@ cudaError_t launch_motif_c4(const MotifBatchArgs& a, unsigned blocks, uint32_t* 
                             cudaStream_t s) {
   k_motif_c4<<<blocks, kC4Threads, 0, s>>>(a, cnt, max_n);
   return cudaGetLastError();
+}
+
+cudaError_t scan_offsets(const uint32_t* in, uint64_t n, int64_t* out, cudaStream_t s);
+
+cudaError_t build_batch_roots(const MotifBatchArgs& a, uint64_t total, uint32_t kmin,
+                              const uint32_t* bounds, int nclass, int sms, BatchRoots* out,
+                              cudaStream_t s) {
+  *out = BatchRoots{};
+  if (total == 0) return cudaSuccess;
+  uint32_t* flag = nullptr;
+  int64_t* pos = nullptr;
+  cudaError_t e = cudaMalloc((void**)&flag, (total + 1) * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&pos, (total + 1) * sizeof(int64_t));
+  const unsigned blocks = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((total + 255) / 256, (uint64_t)sms * 8));
+  for (int c = 0; c <= nclass && e == cudaSuccess; c++) {
+    const bool heavy = c == nclass;
+    const uint32_t lo = heavy ? bounds[nclass - 1] : (c ? bounds[c - 1] : 0u);
+    const uint32_t hi = heavy ? 0u : bounds[c];
+    k_broot_flags<<<blocks, 256, 0, s>>>(a, total, kmin, lo, hi, heavy ? 1 : 0, flag);
+    e = scan_offsets(flag, total, pos, s);
+    int64_t n = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&n, pos + total, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess || n == 0) continue;
+    uint64_t* list = nullptr;
+    e = cudaMalloc((void**)&list, (size_t)n * sizeof(uint64_t));
+    if (e != cudaSuccess) break;
+    if (heavy) {
+      const unsigned wb = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((total + 7) / 8, (uint64_t)sms * 16));
+      k_broot_arcs<<<wb, 256, 0, s>>>(a, total, flag, pos, list);
+      out->heavy = list;
+      out->heavy_count = (uint64_t)n;
+    } else {
+      k_broot_scatter<<<blocks, 256, 0, s>>>(a, total, flag, pos, list);
+      out->roots[c] = list;
+      out->count[c] = (uint64_t)n;
+    }
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(flag);
+  cudaFree(pos);
+  if (e != cudaSuccess) free_batch_roots(out);
+  return e;
+}
+
+void free_batch_roots(BatchRoots* r) {
+  for (auto& p : r->roots) cudaFree(p);
+  cudaFree(r->heavy);
+  *r = BatchRoots{};
 }
 
 }  // namespace gpm

@@ -26,7 +26,27 @@ struct MotifBatchArgs {
   unsigned long long* sums;  // [n_graphs][kNumSums]
   uint32_t chunk;
   uint32_t ratio;
+  // k_motif_k4 only: when idx is set, the tasks are the arcs idx[0, *idx_count)
+  // packed graph << 40 | arc instead of the prefix's arc space
+  const uint64_t* idx;
+  const unsigned long long* idx_count;
 };
+
+// Root lists of the batched local graph search for 4-cliques: the vertices of
+// out-degree class c (kmin <= d+ and bounds[c-1] < d+ <= bounds[c]) of every
+// graph, packed graph << 32 | vertex in (graph, vertex) order, and the arcs of
+// the vertices above the last bound, packed graph << 40 | arc.
+struct BatchRoots {
+  uint64_t* roots[4] = {nullptr, nullptr, nullptr, nullptr};
+  uint64_t count[4] = {0, 0, 0, 0};
+  uint64_t* heavy = nullptr;
+  uint64_t heavy_count = 0;
+};
+// a.graphs / a.n_graphs / a.prefix (the vertex space) describe the batch.
+cudaError_t build_batch_roots(const MotifBatchArgs& a, uint64_t nverts, uint32_t kmin,
+                              const uint32_t* bounds, int nclass, int sms, BatchRoots* out,
+                              cudaStream_t s);
+void free_batch_roots(BatchRoots* r);
 
 uint32_t motif_c4_threads();
 cudaError_t launch_motif_edges(const MotifBatchArgs& a, unsigned blocks, unsigned threads,

@@ -310,6 +310,11 @@ inline unsigned grid_for(uint64_t items_per_warp_units, int sms) {
 
 }  // namespace
 
+// Exclusive scan of n uint32 counts into n + 1 int64 offsets (out[n] = total).
+cudaError_t scan_offsets(const uint32_t* in, uint64_t n, int64_t* out, cudaStream_t s) {
+  return exclusive_scan(in, n, out, s);
+}
+
 cudaError_t validate_csr(const DevCsr& g, bool full, cudaStream_t s, unsigned* flags_out,
                          uint32_t* max_degree_out) {
   unsigned* d = nullptr;

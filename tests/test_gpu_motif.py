@@ -89,12 +89,45 @@ def test_batch_equals_single_and_oracle(k):
             assert single == O.motif_counts(g, k, nthreads=4, method="identities")
         # forced configurations give the same answer
         for opts in ({"chunk": 1, "bsearch_ratio": 1, "warps_per_block": 2},
-                     {"chunk": 64, "bsearch_ratio": 1 << 30, "warps_per_block": 8}):
+                     {"chunk": 64, "bsearch_ratio": 1 << 30, "warps_per_block": 8},
+                     {"chunk": 16, "bsearch_ratio": 8, "warps_per_block": 8, "no_lgs": 1}):
             b = G.gpm_batch_create([h.handle for h in hs], k, opts)
             try:
                 assert np.array_equal(G.gpm_batch_count(b), res)
             finally:
                 G.gpm_batch_free(b)
+    finally:
+        for h in hs:
+            h.close()
+
+
+def test_batch_lgs_all_classes_closed_form():
+    """A batch whose complete graph K_1100 has roots in every out-degree class
+    of the local graph search (the DAG of K_n has out-degrees 0 .. n-1), heavy
+    roots (out-degree > 1024) and arcs whose arc-level local graph exceeds
+    1024 members.  The vertex-induced 4-motifs of K_n are C(n, 4) 4-cliques
+    and nothing else; the other graphs must agree with the oracle and the
+    sorted-set path."""
+    from math import comb
+    gs = [gg.complete(1100), gg.er_graph(3000, 30_000, 41), gg.complete(9), gg.empty(5),
+          gg.rmat_graph(12, 16, 42), gg.complete(300), gg.complete_bipartite(40, 700)]
+    hs = [G.Graph.from_csr(g) for g in gs]
+    try:
+        res = {}
+        for no_lgs in (0, 1):
+            b = G.gpm_batch_create([h.handle for h in hs], 4,
+                                   {"chunk": 16, "bsearch_ratio": 8, "warps_per_block": 8,
+                                    "no_lgs": no_lgs})
+            try:
+                res[no_lgs] = G.gpm_batch_count(b)
+            finally:
+                G.gpm_batch_free(b)
+        assert np.array_equal(res[0], res[1])
+        assert list(map(int, res[0][0])) == [0, 0, 0, 0, 0, comb(1100, 4)]
+        assert list(map(int, res[0][5])) == [0, 0, 0, 0, 0, comb(300, 4)]
+        for i in (1, 2, 3, 4, 6):
+            assert list(map(int, res[0][i])) == O.motif_counts(gs[i], 4, nthreads=8,
+                                                               method="identities")
     finally:
         for h in hs:
             h.close()
