@@ -83,6 +83,7 @@ typedef struct gpm_graph gpm_graph;
                                 needs GPM_DEVICE_PTRS and 64-bit offsets; the caller
                                 keeps them alive and unchanged until gpm_graph_free */
 #define GPM_SKIP_VALIDATE 4u /* trust the input (no sortedness / symmetry check) */
+#define GPM_RELABEL 8u       /* rename the vertices by degree order (see below) */
 
 /*
  * Load an undirected data graph in CSR form (Section 4.2 graph loader).
@@ -92,7 +93,7 @@ typedef struct gpm_graph gpm_graph;
  *                offsets[v+1]); each row strictly ascending, no v in N(v),
  *                and u in N(v) iff v in N(u) (both directions present)
  *   n, nnz       vertices and directed entries (nnz = 2|E|); n < 2^32 - 1
- *   flags        GPM_DEVICE_PTRS | GPM_BORROW | GPM_SKIP_VALIDATE
+ *   flags        GPM_DEVICE_PTRS | GPM_BORROW | GPM_SKIP_VALIDATE | GPM_RELABEL
  *   stream       stream for the copies and the validation kernels
  * The library copies the arrays to device memory it owns (int64 offsets),
  * computes degrees and the maximum degree, and (unless skipped) validates the
@@ -100,6 +101,13 @@ typedef struct gpm_graph gpm_graph;
  * _ASYMMETRIC / _RANGE for the first violation class found.
  * Derived structures (degree-oriented DAG, root task lists) are built on the
  * device the first time a plan needs them and cached with the graph.
+ * GPM_RELABEL (Section 4.2 preprocessing: sorting and renaming the vertices by
+ * degree) renames the validated graph on the device: new vertex i is the
+ * vertex of rank i in ascending (degree, id) order, rows re-sorted.  Counts
+ * do not change; gpm_list translates its matches back to the caller's IDs.
+ * The renamed arrays are owned by the library even under GPM_BORROW (the
+ * caller's arrays are then only read during this call).  Renaming needs
+ * 8 B x (nnz rounded up to a power of two) of temporary device memory.
  */
 gpm_status gpm_load_csr(const void* offsets, int offsets_is_64, const uint32_t* nbrs, uint32_t n,
                         uint64_t nnz, uint32_t flags, void* stream, gpm_graph** out);
@@ -109,6 +117,13 @@ gpm_status gpm_load_csr(const void* offsets, int offsets_is_64, const uint32_t* 
  * out-degree of the degree-oriented DAG (0 until a clique plan built it). */
 gpm_status gpm_graph_info(const gpm_graph* g, uint32_t* n, uint64_t* n_edges, uint32_t* max_degree,
                           uint32_t* max_out_degree);
+
+/* Copy the graph as the library holds it to host memory: offsets int64[n+1],
+ * nbrs uint32[nnz] and, if perm is not NULL, perm uint32[n] = the caller's ID
+ * of every vertex (the identity unless loaded with GPM_RELABEL).  Synchronises
+ * `stream`. */
+gpm_status gpm_graph_export(const gpm_graph* g, int64_t* offsets, uint32_t* nbrs, uint32_t* perm,
+                            void* stream);
 
 /* Release the graph and everything cached with it.  NULL is ignored. */
 void gpm_graph_free(gpm_graph* g);

@@ -22,6 +22,8 @@ cudaError_t launch_small(int family, bool induced, bool list, bool co, const Enu
 cudaError_t occupancy_small(int family, bool induced, bool list, bool co, int threads, size_t smem,
                             int* blocks, int* regs);
 cudaError_t widen_offsets(const int32_t* in, uint64_t count, int64_t* out, cudaStream_t s);
+cudaError_t relabel_by_degree(gpm_graph* G, cudaStream_t s);
+cudaError_t unrename_ids(const gpm_graph* G, uint32_t* ids, uint64_t count, cudaStream_t s);
 uint32_t lgs_warp_max_degree();
 uint32_t lgs_block_max_degree();
 cudaError_t lgs_launch_warp(int k, const LgsArgs& a, unsigned blocks, cudaStream_t s);
@@ -345,6 +347,10 @@ gpm_status gpm_load_csr(const void* offsets, int offsets_is_64, const uint32_t* 
     if (st != GPM_OK) { gpm_graph_free(G); return fail(st, std::string("gpm_load_csr: ") + msg); }
   }
   G->max_degree = maxdeg;
+  if (flags & GPM_RELABEL) {
+    e = relabel_by_degree(G, s);
+    if (e != cudaSuccess) { gpm_graph_free(G); return cuda_fail(e, "gpm_load_csr renaming"); }
+  }
   *out = G;
   return GPM_OK;
 }
@@ -356,6 +362,25 @@ gpm_status gpm_graph_info(const gpm_graph* g, uint32_t* n, uint64_t* n_edges, ui
   if (n_edges) *n_edges = g->g.nnz / 2;
   if (max_degree) *max_degree = g->max_degree;
   if (max_out_degree) *max_out_degree = g->max_out_degree;
+  return GPM_OK;
+}
+
+gpm_status gpm_graph_export(const gpm_graph* g, int64_t* offsets, uint32_t* nbrs, uint32_t* perm,
+                            void* stream) {
+  if (!g || !offsets || (!nbrs && g->g.nnz))
+    return fail(GPM_E_INVALID_ARG, "gpm_graph_export: NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint32_t n = g->g.n;
+  cudaError_t e = cudaMemcpyAsync(offsets, g->g.off, ((size_t)n + 1) * sizeof(int64_t),
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && g->g.nnz)
+    e = cudaMemcpyAsync(nbrs, g->g.nbr, g->g.nnz * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && perm && n && g->perm_d)
+    e = cudaMemcpyAsync(perm, g->perm_d, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "gpm_graph_export");
+  if (perm && !g->perm_d)
+    for (uint32_t v = 0; v < n; v++) perm[v] = v;
   return GPM_OK;
 }
 
@@ -372,6 +397,7 @@ void gpm_graph_free(gpm_graph* g) {
   cudaFree(g->lsrc_d);
   cudaFree(g->ldst_d);
   cudaFree(g->deg32_d);
+  cudaFree(g->perm_d);
   delete g;
 }
 
@@ -581,8 +607,11 @@ gpm_status gpm_list(gpm_plan_t* p, uint32_t* out_dev, uint64_t capacity, uint64_
   Control r;
   gpm_status st = run_plan(p, 0, ~0ull, out_dev, capacity, (cudaStream_t)stream, &r);
   if (st != GPM_OK) return st;
+  const uint64_t written = std::min<uint64_t>(r.result, capacity);
+  const cudaError_t e = unrename_ids(p->graph, out_dev, written * p->k, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gpm_list renaming");
   *n_total = r.result;
-  *n_written = std::min<uint64_t>(r.result, capacity);
+  *n_written = written;
   if (r.result > capacity)
     return fail(GPM_E_CAPACITY, "gpm_list: output truncated to capacity");
   return GPM_OK;

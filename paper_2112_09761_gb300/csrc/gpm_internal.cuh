@@ -90,6 +90,7 @@ struct gpm_graph {
   uint32_t* ldst_d = nullptr;
   uint64_t lower_count = 0;
   uint32_t* deg32_d = nullptr;  // undirected degree of every vertex (lazily built)
+  uint32_t* perm_d = nullptr;   // renamed graphs: the caller's ID of every vertex
   int device = 0;
   int num_sms = 0;
 };

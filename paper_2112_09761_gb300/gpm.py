@@ -24,7 +24,7 @@ STATUS = {0: "GPM_OK", 1: "GPM_E_INVALID_ARG", 2: "GPM_E_UNSORTED", 3: "GPM_E_SE
           7: "GPM_E_UNSUPPORTED_PATTERN", 8: "GPM_E_CAPACITY", 9: "GPM_E_TIMEOUT",
           10: "GPM_E_CUDA", 11: "GPM_E_RANGE"}
 GPM_E_CAPACITY = 8
-GPM_DEVICE_PTRS, GPM_BORROW, GPM_SKIP_VALIDATE = 1, 2, 4
+GPM_DEVICE_PTRS, GPM_BORROW, GPM_SKIP_VALIDATE, GPM_RELABEL = 1, 2, 4, 8
 GPM_COUNT, GPM_LIST = 0, 1
 
 
@@ -73,6 +73,7 @@ def lib():
         L.gpm_pattern_named.argtypes = [ctypes.c_char_p, ctypes.POINTER(gpm_pattern)]
         L.gpm_load_csr.argtypes = [vp, ctypes.c_int, vp, u32, u64, u32, vp, ctypes.POINTER(vp)]
         L.gpm_graph_info.argtypes = [vp, u32p, u64p, u32p, u32p]
+        L.gpm_graph_export.argtypes = [vp, vp, vp, vp, vp]
         L.gpm_graph_free.argtypes = [vp]
         L.gpm_graph_free.restype = None
         L.gpm_plan.argtypes = [vp, ctypes.POINTER(gpm_pattern), ctypes.c_int, ctypes.c_int,
@@ -194,6 +195,17 @@ def gpm_graph_info(g) -> dict:
     _check(lib().gpm_graph_info(g, ctypes.byref(n), ctypes.byref(m), ctypes.byref(d),
                                 ctypes.byref(do)))
     return {"n": n.value, "n_edges": m.value, "max_degree": d.value, "max_out_degree": do.value}
+
+
+def gpm_graph_export(g):
+    """(offsets int64[n+1], nbrs uint32[nnz], perm uint32[n]) as the library holds the graph."""
+    info = gpm_graph_info(g)
+    n, nnz = info["n"], 2 * info["n_edges"]
+    off = np.zeros(n + 1, dtype=np.int64)
+    nbr = np.zeros(max(nnz, 1), dtype=np.uint32)
+    perm = np.zeros(max(n, 1), dtype=np.uint32)
+    _check(lib().gpm_graph_export(g, off.ctypes.data, nbr.ctypes.data, perm.ctypes.data, None))
+    return off, nbr[:nnz], perm[:n]
 
 
 def gpm_graph_free(g) -> None:
