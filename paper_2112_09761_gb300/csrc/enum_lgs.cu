@@ -271,6 +271,9 @@ __device__ __forceinline__ unsigned long long f_small(uint32_t s, const uint32_t
 // each lane walks the members y of S ∩ row_x and adds |S ∩ row_x ∩ row_y|
 // word by word.  S is compacted once; the sets S ∩ row_x are never
 // materialised (rows are triangular, so words start after x and after y).
+// Members are handed to lanes in ascending order through a per-warp counter,
+// so a lane that finishes early takes the next member (the first members
+// carry the most work).  The count fits 32 bits (at most C(1024, 3)).
 template <int NW, bool ST>
 __device__ __forceinline__ unsigned long long f3_lanes(uint32_t S, uint32_t s, const uint32_t* rows,
                                                        uint32_t nw, const WarpScratch& ws,
@@ -279,11 +282,14 @@ __device__ __forceinline__ unsigned long long f3_lanes(uint32_t S, uint32_t s, c
   const uint32_t lane = lane_id();
   compact_set(S, ws.list);
   ws.sb[lane] = S;
+  uint32_t* next = reinterpret_cast<uint32_t*>(ws.cmp);  // unused by this level
+  if (lane == 0) *next = 32;
   __syncwarp();
-  unsigned long long acc = 0;
-  for (uint32_t k = lane; k < s; k += 32) {
+  uint32_t acc = 0;
+  for (uint32_t k = lane; k < s;) {
     const uint32_t x = ws.list[k];
     const uint32_t* rx = rows + x * STRIDE;
+#pragma unroll 2
     for (uint32_t w = (x + 1) >> 5; w < nw; w++) {
       uint32_t t = ws.sb[w] & rx[w];
       if constexpr (ST) wop += 1;
@@ -291,10 +297,12 @@ __device__ __forceinline__ unsigned long long f3_lanes(uint32_t S, uint32_t s, c
         const uint32_t y = w * 32 + __ffs(t) - 1;
         t &= t - 1;
         const uint32_t* ry = rows + y * STRIDE;
+#pragma unroll 2
         for (uint32_t w2 = (y + 1) >> 5; w2 < nw; w2++) acc += __popc(ws.sb[w2] & rx[w2] & ry[w2]);
         if constexpr (ST) wop += nw - ((y + 1) >> 5);
       }
     }
+    k = atomicAdd(next, 1u);
   }
   __syncwarp();
   return acc;
@@ -320,13 +328,15 @@ __device__ __forceinline__ unsigned long long f_set(uint32_t S, const uint32_t* 
     if constexpr (L == 3) return f3_lanes<NW, ST>(S, s, rows, nw, ws, wop);
     if constexpr (L == 2) {
       // edges inside S: lanes take members x, |S ∩ row_x| word by word
+      // (at most C(1024, 2) edges: 32 bits)
       compact_set(S, ws.list);
       ws.sb[lane] = S;
       __syncwarp();
-      unsigned long long acc = 0;
+      uint32_t acc = 0;
       for (uint32_t k = lane; k < s; k += 32) {
         const uint32_t x = ws.list[k];
         const uint32_t* rx = rows + x * STRIDE;
+#pragma unroll 2
         for (uint32_t w = (x + 1) >> 5; w < nw; w++) acc += __popc(ws.sb[w] & rx[w]);
         if constexpr (ST) wop += nw - ((x + 1) >> 5);
       }
