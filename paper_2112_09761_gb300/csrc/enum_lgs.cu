@@ -159,8 +159,9 @@ __global__ void __launch_bounds__(256) k_lgs_warp(LgsArgs a) {
 // One CTA per root with a local graph of 64 < d <= 32*NW members.  Members
 // are laid out in DAG-rank order (sorted by the orientation key (degree, id)),
 // so row_i only holds members after i: rows are upper-triangular.  Rows have
-// a padded stride of NW+1 words (lanes reading word w of different rows hit
-// different banks).  Lane l of a warp holds word l of a candidate set.
+// a padded stride of NW+2 words: every row starts 8-byte aligned, so the
+// innermost word loops load word pairs (64-bit shared-memory loads), and the
+// padding words stay zero.  Lane l of a warp holds word l of a candidate set.
 //
 // Roots are vertices u (members N+(u), a root arc per member), or, for roots
 // too large for shared memory, arcs (u, v) with members N+(u) ∩ N+(v).
@@ -174,18 +175,19 @@ __global__ void __launch_bounds__(256) k_lgs_warp(LgsArgs a) {
 // always run lane-parallel over members, word by word.
 
 // CTA shape per class: NW words per row (members <= 32*NW); 512 threads for
-// the 8- and 16-word classes (several CTAs per SM), 1024 for the 32-word class
-// (one CTA fills the shared memory, so it brings all the warps).
+// the 8- and 16-word classes (several CTAs per SM), 31 warps for the 32-word
+// class (one CTA fills the shared memory, so it brings all the warps it can:
+// its rows and per-warp scratch leave room for 31 warps' scratch, not 32).
 template <int NW>
 struct BlockShape {
-  static constexpr int THREADS = NW >= 32 ? 1024 : 512;
+  static constexpr int THREADS = NW >= 32 ? 992 : 512;
   static constexpr int WARPS = THREADS / 32;
 };
 
 template <int NW>
 struct BlockSmem {
   static constexpr int MAXD = 32 * NW;
-  static constexpr int STRIDE = NW + 1;
+  static constexpr int STRIDE = NW + 2;
   static constexpr int WARPS = BlockShape<NW>::WARPS;
   static constexpr size_t rows = 0;                                           // u32 [MAXD*STRIDE]
   static constexpr size_t aid = rows + sizeof(uint32_t) * MAXD * STRIDE;      // u32 [MAXD] ids (id order)
@@ -240,7 +242,7 @@ template <int L, int NW, bool ST>
 __device__ __forceinline__ unsigned long long f_small(uint32_t s, const uint32_t* rows,
                                                       const WarpScratch& ws,
                                                       unsigned long long& wop) {
-  constexpr int STRIDE = NW + 1;
+  constexpr int STRIDE = NW + 2;
   const uint32_t lane = lane_id();
 #pragma unroll
   for (int h = 0; h < 2; h++) {
@@ -278,7 +280,7 @@ template <int NW, bool ST>
 __device__ __forceinline__ unsigned long long f3_lanes(uint32_t S, uint32_t s, const uint32_t* rows,
                                                        uint32_t nw, const WarpScratch& ws,
                                                        unsigned long long& wop) {
-  constexpr int STRIDE = NW + 1;
+  constexpr int STRIDE = NW + 2;
   const uint32_t lane = lane_id();
   compact_set(S, ws.list);
   ws.sb[lane] = S;
@@ -297,8 +299,15 @@ __device__ __forceinline__ unsigned long long f3_lanes(uint32_t S, uint32_t s, c
         const uint32_t y = w * 32 + __ffs(t) - 1;
         t &= t - 1;
         const uint32_t* ry = rows + y * STRIDE;
-#pragma unroll 2
-        for (uint32_t w2 = (y + 1) >> 5; w2 < nw; w2++) acc += __popc(ws.sb[w2] & rx[w2] & ry[w2]);
+        // word pairs (rows and the set are 8-byte aligned; the word before
+        // an odd start holds no bit after y, words past nw are zero)
+        const uint2* sb2 = reinterpret_cast<const uint2*>(ws.sb);
+        const uint2* rx2 = reinterpret_cast<const uint2*>(rx);
+        const uint2* ry2 = reinterpret_cast<const uint2*>(ry);
+        for (uint32_t p = (y + 1) >> 6; 2 * p < nw; p++) {
+          const uint2 a = sb2[p], b = rx2[p], c = ry2[p];
+          acc += __popc(a.x & b.x & c.x) + __popc(a.y & b.y & c.y);
+        }
         if constexpr (ST) wop += nw - ((y + 1) >> 5);
       }
     }
@@ -314,7 +323,7 @@ __device__ __forceinline__ unsigned long long f_set(uint32_t S, const uint32_t* 
   if constexpr (L == 1) {
     return (unsigned long long)__popc(S);
   } else {
-    constexpr int STRIDE = NW + 1;
+    constexpr int STRIDE = NW + 2;
     const uint32_t lane = lane_id();
     const uint32_t s = __reduce_add_sync(kFull, __popc(S));
     if (s < (uint32_t)L) return 0;
@@ -336,8 +345,12 @@ __device__ __forceinline__ unsigned long long f_set(uint32_t S, const uint32_t* 
       for (uint32_t k = lane; k < s; k += 32) {
         const uint32_t x = ws.list[k];
         const uint32_t* rx = rows + x * STRIDE;
-#pragma unroll 2
-        for (uint32_t w = (x + 1) >> 5; w < nw; w++) acc += __popc(ws.sb[w] & rx[w]);
+        const uint2* sb2 = reinterpret_cast<const uint2*>(ws.sb);
+        const uint2* rx2 = reinterpret_cast<const uint2*>(rx);
+        for (uint32_t p = (x + 1) >> 6; 2 * p < nw; p++) {
+          const uint2 a = sb2[p], b = rx2[p];
+          acc += __popc(a.x & b.x) + __popc(a.y & b.y);
+        }
         if constexpr (ST) wop += nw - ((x + 1) >> 5);
       }
       __syncwarp();
