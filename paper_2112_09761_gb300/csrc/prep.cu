@@ -16,6 +16,10 @@
 #include "setops.cuh"
 
 namespace gpm {
+
+uint64_t sort_capacity(uint64_t n);
+cudaError_t sort_keys(uint64_t* keys, uint64_t n, int sms, cudaStream_t s);
+
 namespace {
 
 constexpr int kScanThreads = 256;
@@ -282,6 +286,25 @@ __global__ void k_lgs_scatter(const uint32_t* __restrict__ flag, const int64_t* 
     if (flag[v]) out[pos[v]] = (uint32_t)v;
 }
 
+// Root order inside a class: descending out-degree (then ascending ID), so the
+// largest local graphs start first and the launch's tail is made of small ones.
+__global__ void k_order_keys(const int64_t* __restrict__ doff, const uint32_t* __restrict__ verts,
+                             uint64_t count, uint64_t* __restrict__ keys) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+    const uint32_t v = verts[i];
+    const uint32_t d = (uint32_t)(doff[v + 1] - doff[v]);
+    keys[i] = ((uint64_t)(0xffffffffu - d) << 32) | v;
+  }
+}
+
+__global__ void k_order_apply(const uint64_t* __restrict__ keys, uint64_t count,
+                              uint32_t* __restrict__ verts) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+    verts[i] = (uint32_t)keys[i];
+}
+
 // out-degree of heavy roots (else 0), then the arc indices of those roots
 __global__ void k_heavy_deg(const int64_t* __restrict__ doff, uint32_t n, uint32_t lo,
                             uint32_t* __restrict__ cnt) {
@@ -426,6 +449,18 @@ cudaError_t build_lgs_classes(gpm_graph* G, uint32_t kmin, const uint32_t* bound
     if (e == cudaSuccess) e = cudaMalloc((void**)&verts[c], ((size_t)total + 1) * sizeof(uint32_t));
     if (e == cudaSuccess && n) k_lgs_scatter<<<blocks, 256, 0, s>>>(flag, pos, n, verts[c]);
     counts[c] = (uint64_t)total;
+    if (e == cudaSuccess && total > 1) {
+      uint64_t* keys = nullptr;
+      e = cudaMalloc((void**)&keys, sort_capacity((uint64_t)total) * sizeof(uint64_t));
+      const unsigned ob = std::max(1u, std::min<unsigned>((unsigned)((total + 255) / 256), G->num_sms * 8u));
+      if (e == cudaSuccess) {
+        k_order_keys<<<ob, 256, 0, s>>>(G->doff_d, verts[c], (uint64_t)total, keys);
+        e = sort_keys(keys, (uint64_t)total, G->num_sms, s);
+      }
+      if (e == cudaSuccess) k_order_apply<<<ob, 256, 0, s>>>(keys, (uint64_t)total, verts[c]);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      cudaFree(keys);
+    }
   }
   *heavy = nullptr;
   *heavy_count = 0;

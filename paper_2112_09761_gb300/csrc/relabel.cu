@@ -138,6 +138,16 @@ unsigned grid_of(uint64_t items, int sms) {
 
 }  // namespace
 
+// Ascending sort of distinct 64-bit keys: keys holds n entries in an array of
+// sort_capacity(n) entries (the rest is overwritten with padding).
+uint64_t sort_capacity(uint64_t n) { return pow2_at_least(n); }
+
+cudaError_t sort_keys(uint64_t* keys, uint64_t n, int sms, cudaStream_t s) {
+  const uint64_t n2 = pow2_at_least(n);
+  if (n2 > n) k_fill_u64<<<grid_of(n2 - n, sms), 256, 0, s>>>(keys, n, n2, ~0ull);
+  return bitonic_sort(keys, n2, sms, s);
+}
+
 // Rename g in place: new arrays (owned), perm_d = old ID of every new vertex.
 cudaError_t relabel_by_degree(gpm_graph* G, cudaStream_t s) {
   const uint32_t n = G->g.n;
