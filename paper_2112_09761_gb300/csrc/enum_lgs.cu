@@ -175,12 +175,13 @@ __global__ void __launch_bounds__(256) k_lgs_warp(LgsArgs a) {
 // always run lane-parallel over members, word by word.
 
 // CTA shape per class: NW words per row (members <= 32*NW); 512 threads for
-// the 8- and 16-word classes (several CTAs per SM), 31 warps for the 32-word
-// class (one CTA fills the shared memory, so it brings all the warps it can:
-// its rows and per-warp scratch leave room for 31 warps' scratch, not 32).
+// the 8-word class (four CTAs per SM), 1024 for the 16-word class (two CTAs
+// per SM fit in shared memory: 64 warps), 31 warps for the 32-word class (one
+// CTA fills the shared memory, so it brings all the warps it can: its rows
+// and per-warp scratch leave room for 31 warps' scratch, not 32).
 template <int NW>
 struct BlockShape {
-  static constexpr int THREADS = NW >= 32 ? 992 : 512;
+  static constexpr int THREADS = NW >= 32 ? 992 : (NW >= 16 ? 1024 : 512);
   static constexpr int WARPS = THREADS / 32;
 };
 
