@@ -87,6 +87,13 @@ def _L():
         lib.og_brute.restype = ctypes.c_uint64
         lib.og_brute.argtypes = [i64p, u32p, ctypes.c_uint32, ctypes.c_uint32,
                                  ctypes.POINTER(ctypes.c_uint8), ctypes.c_uint32, ctypes.c_int]
+        lib.og_automorphisms.restype = ctypes.c_uint64
+        lib.og_automorphisms.argtypes = [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint8),
+                                         ctypes.c_uint32]
+        lib.og_injhom.restype = ctypes.c_uint64
+        lib.og_injhom.argtypes = [i64p, u32p, ctypes.c_uint32, ctypes.c_uint32,
+                                  ctypes.POINTER(ctypes.c_uint8), ctypes.c_uint32, ctypes.c_int,
+                                  ctypes.c_int]
         lib.og_connected_subsets.restype = ctypes.c_uint64
         lib.og_connected_subsets.argtypes = [i64p, u32p, ctypes.c_uint32, ctypes.c_uint32]
         lib.og_identities.restype = ctypes.c_int
@@ -183,6 +190,36 @@ def brute(g, k: int, edges, induced: bool) -> int:
 def brute_named(g, pattern: str, induced: bool) -> int:
     _, k, edges = PATTERNS[pattern]
     return brute(g, k, edges, induced)
+
+
+def _pattern_bytes(edges):
+    pe = np.asarray(edges, dtype=np.uint8).reshape(-1)
+    if len(pe) == 0:
+        pe = np.zeros(2, dtype=np.uint8)
+    return pe
+
+
+def automorphisms(k: int, edges) -> int:
+    """|Aut(P)| by trying every permutation of the k pattern vertices."""
+    pe = _pattern_bytes(edges)
+    return int(_L().og_automorphisms(k, pe.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                     len(edges)))
+
+
+def injhom(g, k: int, edges, induced: bool, nthreads: int = 1) -> int:
+    """O1b: injective homomorphisms P -> G (embeddings before symmetry breaking)."""
+    off, nbr, po, pn = _arrs(g)
+    pe = _pattern_bytes(edges)
+    return int(_L().og_injhom(po, pn, g.n, k, pe.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                              len(edges), int(induced), nthreads))
+
+
+def count_any(g, k: int, edges, induced: bool, nthreads: int = 1) -> int:
+    """Count of Section 2.1 for any pattern: injective homomorphisms / |Aut(P)|."""
+    h = injhom(g, k, edges, induced, nthreads)
+    a = automorphisms(k, edges)
+    assert h % a == 0, "embeddings must split into whole automorphism classes"
+    return h // a
 
 
 def connected_subsets(g, k: int) -> int:

@@ -19,6 +19,10 @@
  *                        intersection / difference (Algorithm 1, Sections 2.2,
  *                        5.4, 6.1).  Per root task, so a sub-range of the task
  *                        list can be compared at full size.
+ *   O1b og_injhom      - any pattern: injective homomorphisms P -> G by plain
+ *                        backtracking (no symmetry breaking), divided by
+ *                        |Aut(P)| (og_automorphisms) gives the count of
+ *                        Section 2.1; mid-size graphs.
  *   O3  og_identities  - closed forms / pattern decompositions (Section 5.4
  *                        counting-only pruning generalised): degrees,
  *                        per-edge triangle counts, wedge co-degrees, and the
@@ -589,6 +593,134 @@ uint64_t og_connected_subsets(const int64_t* off, const uint32_t* nbr, uint32_t 
     for (uint32_t j = (uint32_t)i + 1; j < k; j++) S[j] = S[j - 1] + 1;
   }
   return count;
+}
+
+/* --------------------------------------- O1b injective homomorphisms --- */
+
+/* |Aut(P)|: permutations of the k pattern vertices that map edges to edges
+ * (padj bit i*8+j set iff i~j). */
+uint64_t og_automorphisms(uint32_t k, const uint8_t* pe, uint32_t npe) {
+  if (k < 1 || k > 8) return 0;
+  uint64_t padj = 0;
+  for (uint32_t i = 0; i < npe; i++) {
+    uint32_t a = pe[2 * i], b = pe[2 * i + 1];
+    padj |= 1ULL << (a * 8 + b);
+    padj |= 1ULL << (b * 8 + a);
+  }
+  uint32_t perm[8];
+  for (uint32_t i = 0; i < k; i++) perm[i] = i;
+  uint64_t count = 0;
+  for (;;) {
+    int ok = 1;
+    for (uint32_t i = 0; i < k && ok; i++)
+      for (uint32_t j = i + 1; j < k; j++)
+        if (((padj >> (i * 8 + j)) & 1) != ((padj >> (perm[i] * 8 + perm[j])) & 1)) { ok = 0; break; }
+    count += (uint64_t)ok;
+    int i = (int)k - 2;
+    while (i >= 0 && perm[i] > perm[i + 1]) i--;
+    if (i < 0) break;
+    int j = (int)k - 1;
+    while (perm[j] < perm[i]) j--;
+    uint32_t t = perm[i]; perm[i] = perm[j]; perm[j] = t;
+    for (int a = i + 1, b = (int)k - 1; a < b; a++, b--) { t = perm[a]; perm[a] = perm[b]; perm[b] = t; }
+  }
+  return count;
+}
+
+typedef struct {
+  const og_g* g;
+  uint32_t k;
+  uint64_t padj;
+  int induced;
+  uint32_t ord[8];    /* pattern vertices in visiting order */
+  int anchor[8];      /* a visited pattern neighbour of ord[i] (-1: none) */
+} og_hom;
+
+/* Extend the partial map phi (pattern vertex -> data vertex) of the first i
+ * visited pattern vertices; returns the number of complete injective maps. */
+static uint64_t og_hom_extend(const og_hom* h, uint32_t i, uint32_t* phi) {
+  if (i == h->k) return 1;
+  const uint32_t u = h->ord[i];
+  const uint32_t* cand;
+  uint64_t nc;
+  if (h->anchor[i] >= 0) {
+    cand = ROW(h->g, phi[h->anchor[i]]);
+    nc = DEG(h->g, phi[h->anchor[i]]);
+  } else {
+    cand = NULL;
+    nc = h->g->n;
+  }
+  uint64_t total = 0;
+  for (uint64_t c = 0; c < nc; c++) {
+    const uint32_t x = cand ? cand[c] : (uint32_t)c;
+    int ok = 1;
+    for (uint32_t j = 0; j < i && ok; j++) {
+      const uint32_t w = h->ord[j];
+      if (phi[w] == x) { ok = 0; break; }
+      const int pe = (int)((h->padj >> (u * 8 + w)) & 1);
+      if (pe || h->induced) {
+        const int ge = og_adjacent(h->g, x, phi[w]);
+        if (pe != ge) ok = 0;
+      }
+    }
+    if (!ok) continue;
+    phi[u] = x;
+    total += og_hom_extend(h, i + 1, phi);
+  }
+  return total;
+}
+
+/*
+ * Number of injective maps phi: V(P) -> V(G) with u~w in P => phi(u)~phi(w)
+ * in G (and, if induced, u!~w => phi(u)!~phi(w)): the embeddings of Section
+ * 2.1 before symmetry breaking.  Pattern vertices are visited in BFS order
+ * from vertex 0, each drawing its candidates from the neighbours of an
+ * already mapped pattern neighbour (any vertex when it has none).  The first
+ * vertex's images are split over `nthreads` OpenMP threads.
+ */
+uint64_t og_injhom(const int64_t* off, const uint32_t* nbr, uint32_t n, uint32_t k,
+                   const uint8_t* pe, uint32_t npe, int induced, int nthreads) {
+  og_g g = {n, off, nbr};
+  if (k < 1 || k > 8 || n < k) return 0;
+  og_hom h;
+  h.g = &g;
+  h.k = k;
+  h.padj = 0;
+  h.induced = induced;
+  for (uint32_t i = 0; i < npe; i++) {
+    uint32_t a = pe[2 * i], b = pe[2 * i + 1];
+    h.padj |= 1ULL << (a * 8 + b);
+    h.padj |= 1ULL << (b * 8 + a);
+  }
+  /* BFS order over pattern vertices (restarting at the lowest unvisited) */
+  uint32_t seen = 0, cnt = 0;
+  while (cnt < k) {
+    uint32_t r = 0;
+    while (seen >> r & 1) r++;
+    seen |= 1u << r;
+    h.ord[cnt] = r;
+    h.anchor[cnt] = -1;
+    uint32_t head = cnt++;
+    while (head < cnt) {
+      const uint32_t u = h.ord[head++];
+      for (uint32_t w = 0; w < k; w++)
+        if (!(seen >> w & 1) && ((h.padj >> (u * 8 + w)) & 1)) {
+          seen |= 1u << w;
+          h.ord[cnt] = w;
+          h.anchor[cnt] = (int)u;
+          cnt++;
+        }
+    }
+  }
+  uint64_t total = 0;
+  const uint32_t r0 = h.ord[0];
+#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 16) reduction(+ : total)
+  for (int64_t x = 0; x < (int64_t)n; x++) {
+    uint32_t phi[8];
+    phi[r0] = (uint32_t)x;
+    total += og_hom_extend(&h, 1, phi);
+  }
+  return total;
 }
 
 /* ------------------------------------------------ O3 closed forms --- */

@@ -8,7 +8,11 @@ The oracle is checked against things other than itself:
 * O3 decomposition identities (Section 5.4 counting-only pruning generalised,
   and the edge-induced -> vertex-induced 4-motif inversion) on mid-size graphs;
 * invariants: relabelling, thread count, task-range additivity, the sum of
-  induced 4-motifs = number of connected 4-vertex subsets.
+  induced 4-motifs = number of connected 4-vertex subsets;
+* for any pattern (O1b: injective homomorphisms / |Aut(P)|): group orders of
+  dihedral, star, bipartite and prism patterns, closed forms on complete,
+  cycle, complete-bipartite, star and Petersen graphs, the O1 definition on
+  random graphs and the O2 plans on a mid-size graph.
 """
 import itertools
 import math
@@ -257,3 +261,101 @@ def test_generator_shapes_and_determinism():
             r2 = g.nbrs[g.offsets[v]:g.offsets[v + 1]]
             assert u in r2
     assert gg.csr_checksum(gg.workload("er-10k")) == gg.csr_checksum(g)
+
+
+# ------------------------------------------- any pattern: O1b (injhom / |Aut|)
+
+# patterns beyond the plan families, as (k, edges)
+EXTRA_PATTERNS = {
+    "5-cycle": (5, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 0)]),
+    "5-path": (5, [(0, 1), (1, 2), (2, 3), (3, 4)]),
+    "4-star": (5, [(0, 1), (0, 2), (0, 3), (0, 4)]),
+    "house": (5, [(0, 1), (1, 2), (2, 3), (3, 0), (0, 4), (1, 4)]),
+    "bull": (5, [(0, 1), (1, 2), (2, 0), (0, 3), (1, 4)]),
+    "K2,3": (5, [(0, 2), (0, 3), (0, 4), (1, 2), (1, 3), (1, 4)]),
+    "gem": (5, [(0, 1), (0, 2), (0, 3), (0, 4), (1, 2), (2, 3), (3, 4)]),
+    "prism": (6, [(0, 1), (1, 2), (2, 0), (3, 4), (4, 5), (5, 3), (0, 3), (1, 4), (2, 5)]),
+    "K3,3": (6, [(a, b) for a in range(3) for b in range(3, 6)]),
+    "6-cycle": (6, [(i, (i + 1) % 6) for i in range(6)]),
+}
+
+
+def test_automorphism_group_orders():
+    # the plan families (table of |Aut| used by the oracle's definition)
+    want = {"triangle": 6, "wedge": 2, "4-clique": 24, "diamond": 4, "4-cycle": 8,
+            "tailed-triangle": 2, "3-star": 6, "4-path": 2, "5-clique": 120}
+    for name, a in want.items():
+        _, k, e = O.PATTERNS[name]
+        assert O.automorphisms(k, e) == a, name
+    # dihedral, star, bipartite and product groups
+    want = {"5-cycle": 10, "5-path": 2, "4-star": 24, "house": 2, "bull": 2, "K2,3": 12,
+            "gem": 2, "prism": 12, "K3,3": 72, "6-cycle": 12}
+    for name, a in want.items():
+        k, e = EXTRA_PATTERNS[name]
+        assert O.automorphisms(k, e) == a, name
+
+
+@pytest.mark.parametrize("n", [6, 7, 9])
+def test_any_pattern_on_complete_graphs(n):
+    # in K_n every injective map is an embedding: n!/(n-k)! / |Aut(P)| edge-induced
+    # matches; vertex-induced, only complete patterns occur
+    for name, (k, e) in EXTRA_PATTERNS.items():
+        if k > n:
+            continue
+        falling = math.factorial(n) // math.factorial(n - k)
+        assert O.count_any(gg.complete(n), k, e, False) == falling // O.automorphisms(k, e), name
+        assert O.count_any(gg.complete(n), k, e, True) == 0, name
+    assert O.count_any(gg.complete(n), 5, O.PATTERNS["5-clique"][2], True) == C(n, 5)
+
+
+def test_any_pattern_closed_forms():
+    # cycles and paths in a cycle graph C_m: m copies of each path shorter than m,
+    # one m-cycle
+    for m in (7, 9, 12):
+        g = gg.cycle(m)
+        assert O.count_any(g, 5, EXTRA_PATTERNS["5-path"][1], False) == m
+        assert O.count_any(g, 5, EXTRA_PATTERNS["5-path"][1], True) == m
+        assert O.count_any(g, 5, EXTRA_PATTERNS["5-cycle"][1], False) == 0
+    assert O.count_any(gg.cycle(5), 5, EXTRA_PATTERNS["5-cycle"][1], True) == 1
+    # K_{a,b}: no odd cycle; 6-cycles = C(a,3) C(b,3) * 3! * 3! / (2 * 6) ... counted
+    # as ordered alternations: C(a,3) C(b,3) * 6; K2,3 copies = C(a,2) C(b,3) + C(a,3) C(b,2)
+    for a, b in ((3, 4), (4, 5), (5, 5)):
+        g = gg.complete_bipartite(a, b)
+        assert O.count_any(g, 5, EXTRA_PATTERNS["5-cycle"][1], False) == 0
+        assert O.count_any(g, 6, EXTRA_PATTERNS["6-cycle"][1], False) == C(a, 3) * C(b, 3) * 6
+        assert O.count_any(g, 5, EXTRA_PATTERNS["K2,3"][1], True) == C(a, 2) * C(b, 3) + C(a, 3) * C(b, 2)
+        assert O.count_any(g, 6, EXTRA_PATTERNS["K3,3"][1], True) == C(a, 3) * C(b, 3)
+    # the Petersen graph: 12 five-cycles, 10 six-cycles, no 4-cycle, 15 edges
+    outer = [(i, (i + 1) % 5) for i in range(5)]
+    inner = [(5 + i, 5 + (i + 2) % 5) for i in range(5)]
+    spokes = [(i, i + 5) for i in range(5)]
+    pet = gg.from_edges(10, outer + inner + spokes)
+    assert O.count_any(pet, 5, EXTRA_PATTERNS["5-cycle"][1], False) == 12
+    assert O.count_any(pet, 6, EXTRA_PATTERNS["6-cycle"][1], False) == 10
+    assert O.count_any(pet, 4, O.PATTERNS["4-cycle"][2], False) == 0
+    # a star K_{1,m}: C(m, 4) four-stars, both modes
+    assert O.count_any(gg.star(9), 5, EXTRA_PATTERNS["4-star"][1], False) == C(9, 4)
+    assert O.count_any(gg.star(9), 5, EXTRA_PATTERNS["4-star"][1], True) == C(9, 4)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_any_pattern_equals_definition(seed):
+    # O1b against the O1 definition (k-subsets x edge subsets x isomorphism)
+    g = gg.gnp_graph(11, 0.5, 100 + seed)
+    for name, (k, e) in EXTRA_PATTERNS.items():
+        if k == 6 and seed > 1:
+            continue
+        for induced in (False, True):
+            assert O.count_any(g, k, e, induced) == O.brute(g, k, e, induced), (name, induced)
+
+
+def test_any_pattern_equals_plan_families():
+    # O1b against the O2 nested-loop plans, mid-size graph, thread count invariant
+    g = gg.gnp_graph(70, 0.25, 8)
+    for name in SMALL_PATTERNS:
+        _, k, e = O.PATTERNS[name]
+        for induced in (False, True):
+            want = O.count(g, name, induced=induced, nthreads=4)
+            assert O.count_any(g, k, e, induced, nthreads=4) == want, (name, induced)
+    k, e = EXTRA_PATTERNS["house"]
+    assert O.count_any(g, k, e, True, nthreads=1) == O.count_any(g, k, e, True, nthreads=4)
