@@ -145,7 +145,7 @@ typedef struct gpm_plan_opts {
   uint32_t collect_stats;    /* 1 = count algorithmic bytes / set operations (slower) */
   uint32_t no_lgs;           /* 1 = cliques (and batched 4-cliques) without local graph
                                 search (sorted sets only) */
-  uint32_t reserved[1];
+  uint32_t generic_plan;     /* 1 = run the generic interpreter even for a named family */
 } gpm_plan_opts;
 
 /*
@@ -156,11 +156,20 @@ typedef struct gpm_plan_opts {
  *   opts      NULL for automatic choices
  * The pattern is identified up to isomorphism with one of the named families
  * (k-clique up to k = 8, diamond, 4-cycle, tailed-triangle, 3-star, 4-path,
- * wedge); anything else returns GPM_E_UNSUPPORTED_PATTERN.  The plan fixes the
- * matching order, the symmetry order, the root task list Omega (reduced to
- * v1 > v2 when the symmetry order allows, Section 7.2 (2)), the per-warp DFS
- * buffers (Section 7.2 (3)) and the grid; it builds the DAG / task lists on
- * the device if the graph has not cached them yet.
+ * wedge), which have hand-written plans.  Any other connected pattern of 3 to
+ * 8 vertices (or any pattern with opts->generic_plan) gets a search plan from
+ * the pattern analyzer: the matching order with the least estimated
+ * neighbour-list reading over all valid orders, and a symmetry order built
+ * along it from the pattern's automorphisms (each vertex the largest of its
+ * orbit under the automorphisms fixing the earlier ones), run by the generic
+ * interpreter.  Disconnected patterns, or fewer than 3 or more than 8
+ * vertices, return GPM_E_UNSUPPORTED_PATTERN.  The plan fixes the matching
+ * order, the symmetry order, the root task list Omega (reduced to v1 > v2 when
+ * the symmetry order allows, Section 7.2 (2)), the per-warp DFS buffers
+ * (Section 7.2 (3)) and the grid; it builds the DAG / task lists on the device
+ * if the graph has not cached them yet.  Listings write each match as k
+ * uint32, entry i being the data vertex matched to pattern vertex i for
+ * generic plans and the plan's matching order for the named families.
  */
 gpm_status gpm_plan(gpm_graph* g, const gpm_pattern* pattern, int induced, int mode,
                     const gpm_plan_opts* opts, void* stream, gpm_plan_t** out);
@@ -170,6 +179,20 @@ gpm_status gpm_plan(gpm_graph* g, const gpm_pattern* pattern, int induced, int m
  * (by v1 then v2), and all directed CSR entries for tailed-triangle / 3-star /
  * wedge (CSR order).  This order defines the task ranges of gpm_count_range. */
 gpm_status gpm_plan_info(const gpm_plan_t* p, uint64_t* n_tasks, uint32_t* k);
+
+/* The plan as text (NUL-terminated, at most len bytes with the NUL): its
+ * family and, for generic plans, the matching order as pattern vertices
+ * ("order: u1 u0 u2 ..."), the symmetry order over matching positions
+ * ("symmetry: v0>v1 v2>v3", vi = the data vertex at position i), the root
+ * task list and the induced mode.  GPM_E_CAPACITY if the text was cut. */
+gpm_status gpm_plan_describe(const gpm_plan_t* p, char* buf, size_t len);
+
+/* The search plan gpm_plan would choose for `pattern` on a graph of n
+ * vertices and nnz directed entries (the cost model's inputs), as the same
+ * text, without a graph or a GPU: host-side pattern analysis only.  generic =
+ * 1 analyses named families as gpm_plan does with opts->generic_plan. */
+gpm_status gpm_pattern_describe(const gpm_pattern* pattern, int induced, uint32_t n, uint64_t nnz,
+                                int generic, char* buf, size_t len);
 
 /* Count all matches (Section 4.1 count()).  *out_count is a host uint64.
  * Synchronises `stream`. */

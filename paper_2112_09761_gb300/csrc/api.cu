@@ -23,6 +23,12 @@ cudaError_t occupancy_small(int family, bool induced, bool list, bool co, int th
                             int* blocks, int* regs);
 cudaError_t widen_offsets(const int32_t* in, uint64_t count, int64_t* out, cudaStream_t s);
 cudaError_t relabel_by_degree(gpm_graph* G, cudaStream_t s);
+cudaError_t launch_generic(bool list, const EnumArgs& a, dim3 grid, dim3 block, size_t smem,
+                           cudaStream_t s);
+cudaError_t occupancy_generic(bool list, int threads, size_t smem, int* blocks, int* regs);
+bool analyze_pattern(uint32_t k, const std::vector<std::pair<int, int>>& edges, int induced,
+                     double n, double avg_degree, GenTable* T, std::string* why);
+std::string describe_gen(const GenTable& T);
 cudaError_t unrename_ids(const gpm_graph* G, uint32_t* ids, uint64_t count, cudaStream_t s);
 uint32_t lgs_warp_max_degree();
 uint32_t lgs_block_max_degree();
@@ -133,6 +139,7 @@ uint32_t plan_levels(int family, uint32_t k, bool induced, bool list, bool co) {
     case kStar3: return induced ? (list ? 2 : 1) : 0;
     case kPath4: return induced ? (list ? 3 : 2) : 0;
     case kWedge: return (induced && list) ? 1 : 0;
+    case kGeneric: return k - 1;  // positions 2..k-1 and one scratch level
     default: return 0;
   }
 }
@@ -148,6 +155,7 @@ TaskKind task_kind_of(int family) {
 cudaError_t occupancy(const gpm_plan_t* p, int threads, size_t smem, int* blocks, int* regs) {
   const bool list = p->mode == GPM_LIST;
   if (p->family == kClique) return occupancy_clique((int)p->k, list, threads, smem, blocks, regs);
+  if (p->family == kGeneric) return occupancy_generic(list, threads, smem, blocks, regs);
   return occupancy_small(p->family, p->induced, list, p->count_only, threads, smem, blocks, regs);
 }
 
@@ -182,10 +190,12 @@ cudaError_t launch_enum(gpm_plan_t* p, uint64_t lo, uint64_t hi, uint32_t* list_
   a.arc_lo = 0;
   a.arc_hi = 0;
   a.idx_count = nullptr;
+  a.gen = p->gen_d;
   const dim3 grid(p->cfg.blocks), block(p->cfg.warps_per_block * 32);
   const size_t smem = enum_smem_bytes(p);
   const bool list = p->mode == GPM_LIST;
   if (p->family == kClique) return launch_clique((int)p->k, list, a, grid, block, smem, s);
+  if (p->family == kGeneric) return launch_generic(list, a, grid, block, smem, s);
   return launch_small(p->family, p->induced, list, p->count_only, a, grid, block, smem, s);
 }
 
@@ -405,14 +415,32 @@ gpm_status gpm_plan(gpm_graph* G, const gpm_pattern* pattern, int induced, int m
                     const gpm_plan_opts* opts, void* stream, gpm_plan_t** out) {
   if (!G || !pattern || !out) return fail(GPM_E_INVALID_ARG, "gpm_plan: NULL argument");
   if (mode != GPM_COUNT && mode != GPM_LIST) return fail(GPM_E_INVALID_ARG, "gpm_plan: bad mode");
-  int family = 0;
-  uint32_t k = 0;
-  if (!identify(pattern, &family, &k))
-    return fail(GPM_E_UNSUPPORTED_PATTERN, "gpm_plan: pattern matches no supported plan family");
   cudaStream_t s = (cudaStream_t)stream;
   gpm_plan_opts o;
   memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
+  int family = 0;
+  uint32_t k = 0;
+  GenTable gt{};
+  if (!identify(pattern, &family, &k) || o.generic_plan) {
+    // any other connected pattern: the analyzer's search plan for the
+    // generic interpreter
+    if (pattern->k < 3 || pattern->k > (uint32_t)kGenMaxK || pattern->n_edges > 28)
+      return fail(GPM_E_UNSUPPORTED_PATTERN, "gpm_plan: patterns have 3 to 8 vertices");
+    std::vector<std::pair<int, int>> edges;
+    for (uint32_t i = 0; i < pattern->n_edges; i++) {
+      const int a = pattern->edges[i][0], b = pattern->edges[i][1];
+      edges.push_back({std::min(a, b), std::max(a, b)});
+    }
+    std::sort(edges.begin(), edges.end());
+    edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
+    std::string why;
+    const double n = G->g.n, d = G->g.n ? (double)G->g.nnz / G->g.n : 0.0;
+    if (!analyze_pattern(pattern->k, edges, induced ? 1 : 0, n, d, &gt, &why))
+      return fail(GPM_E_UNSUPPORTED_PATTERN, "gpm_plan: " + why);
+    family = kGeneric;
+    k = pattern->k;
+  }
   gpm_plan_t* p = new gpm_plan_t();
   p->graph = G;
   p->family = family;
@@ -420,7 +448,13 @@ gpm_status gpm_plan(gpm_graph* G, const gpm_pattern* pattern, int induced, int m
   p->induced = (family == kClique) ? 0 : (induced ? 1 : 0);
   p->mode = mode;
   p->count_only = o.no_count_only ? 0 : 1;
-  p->task_kind = task_kind_of(family);
+  p->task_kind = family == kGeneric ? (gt.root_lower ? kTasksLower : kTasksAll) : task_kind_of(family);
+  if (family == kGeneric) {
+    p->gen = gt;
+    cudaError_t eg = cudaMalloc((void**)&p->gen_d, sizeof(GenTable));
+    if (eg == cudaSuccess) eg = cudaMemcpy(p->gen_d, &gt, sizeof(GenTable), cudaMemcpyHostToDevice);
+    if (eg != cudaSuccess) { gpm_plan_free(p); return cuda_fail(eg, "gpm_plan search plan"); }
+  }
   cudaError_t e = cudaSuccess;
   uint32_t bound = G->max_degree;  // per-level buffer bound
   switch (p->task_kind) {
@@ -452,6 +486,7 @@ gpm_status gpm_plan(gpm_graph* G, const gpm_pattern* pattern, int induced, int m
   // else 512 entries (larger tasks spill to the per-warp HBM slice)
   c.smem_cap = c.levels ? std::min<uint32_t>(std::max<uint32_t>(bound, 1u), 512u) : 0u;
   c.gstack_cap = (c.levels && bound > c.smem_cap) ? bound : 0u;
+  if (family == kGeneric && c.gstack_cap) c.smem_cap = 0;  // all its levels live in one place
   int occ = 0, regs = 0;
   e = occupancy(p, c.warps_per_block * 32, enum_smem_bytes(p), &occ, &regs);
   if (e != cudaSuccess) { delete p; return cuda_fail(e, "gpm_plan occupancy"); }
@@ -527,6 +562,52 @@ gpm_status gpm_plan_info(const gpm_plan_t* p, uint64_t* n_tasks, uint32_t* k) {
   if (n_tasks) *n_tasks = p->tasks.count;
   if (k) *k = p->k;
   return GPM_OK;
+}
+
+gpm_status gpm_pattern_describe(const gpm_pattern* pattern, int induced, uint32_t n, uint64_t nnz,
+                                int generic, char* buf, size_t len) {
+  if (!pattern || !buf || len == 0) return fail(GPM_E_INVALID_ARG, "gpm_pattern_describe: bad argument");
+  int family = 0;
+  uint32_t k = 0;
+  std::string d;
+  if (identify(pattern, &family, &k) && !generic) {
+    static const char* kNames[] = {"", "k-clique", "diamond", "4-cycle", "tailed-triangle",
+                                   "3-star", "4-path", "wedge", "generic"};
+    d = std::string("family: ") + kNames[family] + " (k = " + std::to_string(k) + ")";
+  } else {
+    if (pattern->k < 3 || pattern->k > (uint32_t)kGenMaxK || pattern->n_edges > 28)
+      return fail(GPM_E_UNSUPPORTED_PATTERN, "gpm_pattern_describe: patterns have 3 to 8 vertices");
+    std::vector<std::pair<int, int>> edges;
+    for (uint32_t i = 0; i < pattern->n_edges; i++) {
+      const int a = pattern->edges[i][0], b = pattern->edges[i][1];
+      edges.push_back({std::min(a, b), std::max(a, b)});
+    }
+    std::sort(edges.begin(), edges.end());
+    edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
+    GenTable gt{};
+    std::string why;
+    if (!analyze_pattern(pattern->k, edges, induced ? 1 : 0, (double)n, n ? (double)nnz / n : 0.0,
+                         &gt, &why))
+      return fail(GPM_E_UNSUPPORTED_PATTERN, "gpm_pattern_describe: " + why);
+    d = "family: generic (k = " + std::to_string(pattern->k) + "); " + describe_gen(gt);
+  }
+  const size_t nb = std::min(len - 1, d.size());
+  memcpy(buf, d.data(), nb);
+  buf[nb] = 0;
+  return d.size() < len ? GPM_OK : fail(GPM_E_CAPACITY, "gpm_pattern_describe: text truncated");
+}
+
+gpm_status gpm_plan_describe(const gpm_plan_t* p, char* buf, size_t len) {
+  if (!p || !buf || len == 0) return fail(GPM_E_INVALID_ARG, "gpm_plan_describe: bad argument");
+  static const char* kNames[] = {"", "k-clique", "diamond", "4-cycle", "tailed-triangle",
+                                 "3-star", "4-path", "wedge", "generic"};
+  std::string d = std::string("family: ") + kNames[p->family] + " (k = " + std::to_string(p->k) + ")";
+  if (p->family == kGeneric) d += "; " + describe_gen(p->gen);
+  else if (p->lgs) d += "; local graph search";
+  const size_t nb = std::min(len - 1, d.size());
+  memcpy(buf, d.data(), nb);
+  buf[nb] = 0;
+  return d.size() < len ? GPM_OK : fail(GPM_E_CAPACITY, "gpm_plan_describe: text truncated");
 }
 
 }  // extern "C"
@@ -635,6 +716,7 @@ void gpm_plan_free(gpm_plan_t* p) {
   cudaFree(p->heavy_idx);
   cudaFree(p->overflow_d);
   cudaFree(p->wedge_cnt);
+  cudaFree(p->gen_d);
   if (p->host_pinned) cudaFreeHost(p->host_pinned);
   delete p;
 }

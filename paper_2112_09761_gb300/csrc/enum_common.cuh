@@ -35,6 +35,7 @@ struct EnumArgs {
   const uint64_t* idx;  // null, or: task t is arc idx[t] (counted if in [arc_lo, arc_hi))
   uint64_t arc_lo, arc_hi;
   const unsigned long long* idx_count;  // null, or the device-side length of idx
+  const GenTable* gen;  // generic plans: the search plan (device memory), else null
 };
 
 // One graph of a batch as the local-graph-search kernels see it.

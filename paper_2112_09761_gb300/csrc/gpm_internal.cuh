@@ -17,7 +17,25 @@ enum Family : int {
   kTailedTriangle = 4,  // triangle v1 v2 v3 (v3 < v2) + tail v4 on v1
   kStar3 = 5,           // centre v1, leaves v2 > v3 > v4
   kPath4 = 6,           // v3 - v1 - v2 - v4 with v1 > v2
-  kWedge = 7            // centre v1, ends v2 > v3
+  kWedge = 7,           // centre v1, ends v2 > v3
+  kGeneric = 8          // any connected pattern: the generic interpreter (GenTable)
+};
+
+// Search plan of the generic interpreter (Section 4.2 pattern analyzer): the
+// matching order and the symmetry order of a connected pattern with 3..8
+// vertices, as per-position lists of earlier positions.  Position t's
+// candidates are the common neighbours of the matches of E[t], below the
+// matches of U[t], distinct from the matches of N[t] and, vertex-induced,
+// adjacent to none of them.
+constexpr int kGenMaxK = 8;
+struct GenTable {
+  uint32_t k;
+  uint32_t induced;
+  uint32_t root_lower;             // symmetry order holds v0 > v1: root tasks are pairs v1 < v0
+  uint8_t order[kGenMaxK];         // pattern vertex matched at each position
+  uint8_t nE[kGenMaxK], E[kGenMaxK][kGenMaxK];  // earlier positions adjacent in the pattern
+  uint8_t nN[kGenMaxK], N[kGenMaxK][kGenMaxK];  // earlier positions not adjacent
+  uint8_t nU[kGenMaxK], U[kGenMaxK][kGenMaxK];  // earlier positions s with v_t < v_s
 };
 
 // Root task lists (Section 7.2 (2) edgelist reduction).
@@ -125,6 +143,9 @@ struct gpm_plan_s {
   unsigned wedge_blocks = 0;
   unsigned lgs_warp_blocks = 0;
   unsigned lgs_bps[4] = {1, 1, 1, 1};  // resident CTAs per SM of each CTA class
+  // generic plans: the search plan (host copy and device copy)
+  gpm::GenTable gen{};
+  gpm::GenTable* gen_d = nullptr;
 };
 
 namespace gpm {

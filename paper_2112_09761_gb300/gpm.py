@@ -47,7 +47,7 @@ class gpm_plan_opts(ctypes.Structure):
     _fields_ = [("warps_per_block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
                 ("chunk", ctypes.c_uint32), ("bsearch_ratio", ctypes.c_uint32),
                 ("no_count_only", ctypes.c_uint32), ("collect_stats", ctypes.c_uint32),
-                ("no_lgs", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 1)]
+                ("no_lgs", ctypes.c_uint32), ("generic_plan", ctypes.c_uint32)]
 
 
 _lib = None
@@ -79,6 +79,9 @@ def lib():
         L.gpm_plan.argtypes = [vp, ctypes.POINTER(gpm_pattern), ctypes.c_int, ctypes.c_int,
                                ctypes.POINTER(gpm_plan_opts), vp, ctypes.POINTER(vp)]
         L.gpm_plan_info.argtypes = [vp, u64p, u32p]
+        L.gpm_plan_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+        L.gpm_pattern_describe.argtypes = [ctypes.POINTER(gpm_pattern), ctypes.c_int, u32, u64,
+                                           ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t]
         L.gpm_count.argtypes = [vp, u64p, vp]
         L.gpm_count_range.argtypes = [vp, u64, u64, u64p, vp]
         L.gpm_list.argtypes = [vp, vp, u64, u64p, u64p, vp]
@@ -232,6 +235,23 @@ def gpm_plan_info(p) -> dict:
     nt, k = ctypes.c_uint64(), ctypes.c_uint32()
     _check(lib().gpm_plan_info(p, ctypes.byref(nt), ctypes.byref(k)))
     return {"n_tasks": nt.value, "k": k.value}
+
+
+def gpm_plan_describe(p) -> str:
+    buf = ctypes.create_string_buffer(1024)
+    _check(lib().gpm_plan_describe(p, buf, len(buf)))
+    return buf.value.decode()
+
+
+def gpm_pattern_describe(pattern, induced: bool = False, n: int = 0, nnz: int = 0,
+                         generic: bool = False) -> str:
+    """Host-side pattern analysis: the search plan text gpm_plan would use."""
+    if isinstance(pattern, str):
+        pattern = gpm_pattern_named(pattern)
+    buf = ctypes.create_string_buffer(1024)
+    _check(lib().gpm_pattern_describe(ctypes.byref(pattern), int(bool(induced)), n, nnz,
+                                      int(bool(generic)), buf, len(buf)))
+    return buf.value.decode()
 
 
 def gpm_count(p, stream=None) -> int:
