@@ -146,6 +146,10 @@ typedef struct gpm_plan_opts {
   uint32_t no_lgs;           /* 1 = cliques (and batched 4-cliques) without local graph
                                 search (sorted sets only) */
   uint32_t generic_plan;     /* 1 = run the generic interpreter even for a named family */
+  uint32_t vertex_parallel;  /* 1 = root tasks are vertices (Section 5.1 vertex parallelism):
+                                a warp takes a vertex v1 and walks its root pairs (v1, v2)
+                                from its row, no task list Omega is built, task ranges are
+                                vertex ranges; cliques then use the sorted-set kernel */
 } gpm_plan_opts;
 
 /*
@@ -177,7 +181,10 @@ gpm_status gpm_plan(gpm_graph* g, const gpm_pattern* pattern, int induced, int m
 /* Number of root tasks |Omega| of the plan: DAG arcs for cliques (listed by
  * source then destination ID), pairs v1 > v2 for diamond / 4-cycle / 4-path
  * (by v1 then v2), and all directed CSR entries for tailed-triangle / 3-star /
- * wedge (CSR order).  This order defines the task ranges of gpm_count_range. */
+ * wedge (CSR order); generic plans use pairs v1 > v2 when their symmetry order
+ * holds v0 > v1, else all directed entries.  This order defines the task
+ * ranges of gpm_count_range.  With opts->vertex_parallel the tasks are the n
+ * vertices instead (vertex v roots the pairs of its row). */
 gpm_status gpm_plan_info(const gpm_plan_t* p, uint64_t* n_tasks, uint32_t* k);
 
 /* The plan as text (NUL-terminated, at most len bytes with the NUL): its

@@ -191,6 +191,8 @@ cudaError_t launch_enum(gpm_plan_t* p, uint64_t lo, uint64_t hi, uint32_t* list_
   a.arc_hi = 0;
   a.idx_count = nullptr;
   a.gen = p->gen_d;
+  a.vertex_tasks = p->vertex_tasks ? 1u : 0u;
+  a.vkind = (uint32_t)p->task_kind;
   const dim3 grid(p->cfg.blocks), block(p->cfg.warps_per_block * 32);
   const size_t smem = enum_smem_bytes(p);
   const bool list = p->mode == GPM_LIST;
@@ -457,6 +459,10 @@ gpm_status gpm_plan(gpm_graph* G, const gpm_pattern* pattern, int induced, int m
   }
   cudaError_t e = cudaSuccess;
   uint32_t bound = G->max_degree;  // per-level buffer bound
+  // vertex parallelism: the root tasks of a vertex are walked from its row,
+  // so no task list is built (local graph search is vertex-rooted already
+  // and keeps arc ranges, so it is not combined with it)
+  p->vertex_tasks = o.vertex_parallel != 0;
   switch (p->task_kind) {
     case kTasksDag:
       e = build_dag(G, s);
@@ -465,16 +471,17 @@ gpm_status gpm_plan(gpm_graph* G, const gpm_pattern* pattern, int induced, int m
       bound = G->max_out_degree;
       break;
     case kTasksLower:
-      e = build_lower(G, s);
+      if (!p->vertex_tasks) e = build_lower(G, s);
       p->csr = G->g;
       p->tasks = DevTasks{G->lsrc_d, G->ldst_d, G->lower_count};
       break;
     case kTasksAll:
-      e = build_rows(G, s);
+      if (!p->vertex_tasks) e = build_rows(G, s);
       p->csr = G->g;
       p->tasks = DevTasks{G->row_d, G->nbr_d, G->g.nnz};
       break;
   }
+  if (p->vertex_tasks) p->tasks = DevTasks{nullptr, nullptr, G->g.n};
   if (e != cudaSuccess) { delete p; return cuda_fail(e, "gpm_plan preprocessing"); }
 
   LaunchCfg& c = p->cfg;
@@ -514,7 +521,7 @@ gpm_status gpm_plan(gpm_graph* G, const gpm_pattern* pattern, int induced, int m
     e = cudaMalloc((void**)&p->gstack_d, p->gstack_bytes);
     if (e != cudaSuccess) { delete p; return cuda_fail(e, "gpm_plan DFS buffers"); }
   }
-  if (family == kClique && mode == GPM_COUNT && k >= 4 && !o.no_lgs) {
+  if (family == kClique && mode == GPM_COUNT && k >= 4 && !o.no_lgs && !p->vertex_tasks) {
     p->lgs = true;
     const uint32_t bounds[4] = {lgs_warp_max_degree(), 256, 512, lgs_block_max_degree()};
     e = build_lgs_classes(G, k - 1, bounds, 4, p->lgs_verts, p->lgs_count, &p->heavy_idx,

@@ -36,6 +36,11 @@ struct EnumArgs {
   uint64_t arc_lo, arc_hi;
   const unsigned long long* idx_count;  // null, or the device-side length of idx
   const GenTable* gen;  // generic plans: the search plan (device memory), else null
+  // vertex parallelism (Section 5.1): task t is vertex lo + t and its root
+  // tasks (v1, v2) are v2 in row v1 of g (vkind = kTasksLower: only v2 < v1);
+  // no task list Omega exists
+  uint32_t vertex_tasks;
+  uint32_t vkind;
 };
 
 // One graph of a batch as the local-graph-search kernels see it.
@@ -192,6 +197,14 @@ __device__ __forceinline__ void task_loop(const EnumArgs& a) {
     const uint64_t end = min((uint64_t)start + c, ntask);
     for (uint64_t t = start; t < end; t++) {
       uint64_t e = a.lo + t;
+      if (a.vertex_tasks) {
+        const uint32_t v1 = (uint32_t)e;
+        const uint32_t* R = row_of(a.g, v1);
+        const uint32_t d = deg_of(a.g, v1);
+        const uint32_t nr = (a.vkind == kTasksLower) ? warp_count_less(R, d, v1) : d;
+        for (uint32_t j = 0; j < nr; j++) acc += Plan::run(a, v1, R[j], sbuf, gbuf);
+        continue;
+      }
       if (a.idx) {
         e = a.idx[t];
         if (e < a.arc_lo || e >= a.arc_hi) continue;  // warp-uniform
@@ -200,7 +213,8 @@ __device__ __forceinline__ void task_loop(const EnumArgs& a) {
       const uint32_t v2 = a.dst[e];
       acc += Plan::run(a, v1, v2, sbuf, gbuf);
     }
-    if (a.stats && lane == 0) atomicAdd(&a.stats[0], 8ull * (end - start));  // (src, dst)
+    if (a.stats && lane == 0)  // (src, dst) per task, or the offsets of a task vertex
+      atomicAdd(&a.stats[0], (a.vertex_tasks ? 16ull : 8ull) * (end - start));
   }
   if (lane == 0 && acc) atomicAdd(&s_acc, acc);
   __syncthreads();

@@ -146,6 +146,8 @@ struct gpm_plan_s {
   // generic plans: the search plan (host copy and device copy)
   gpm::GenTable gen{};
   gpm::GenTable* gen_d = nullptr;
+  // vertex parallelism: root tasks are vertices (no task list built)
+  bool vertex_tasks = false;
 };
 
 namespace gpm {

@@ -47,7 +47,8 @@ class gpm_plan_opts(ctypes.Structure):
     _fields_ = [("warps_per_block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
                 ("chunk", ctypes.c_uint32), ("bsearch_ratio", ctypes.c_uint32),
                 ("no_count_only", ctypes.c_uint32), ("collect_stats", ctypes.c_uint32),
-                ("no_lgs", ctypes.c_uint32), ("generic_plan", ctypes.c_uint32)]
+                ("no_lgs", ctypes.c_uint32), ("generic_plan", ctypes.c_uint32),
+                ("vertex_parallel", ctypes.c_uint32)]
 
 
 _lib = None
