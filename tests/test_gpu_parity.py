@@ -220,8 +220,14 @@ def test_pattern_given_by_edges_is_identified():
         # a 4-cycle
         p = G.pattern_from_edges(4, [(0, 2), (2, 1), (1, 3), (3, 0)])
         assert G.gpm_count(h.plan(p, induced=True)) == O.count(g, "4-cycle", induced=True)
+        # a pattern outside the named families goes to the generic interpreter
+        c5 = [(0, 1), (1, 2), (2, 3), (3, 4), (4, 0)]
+        p = h.plan(G.pattern_from_edges(5, c5))
+        assert G.gpm_plan_describe(p).startswith("family: generic")
+        assert G.gpm_count(p) == O.count_any(g, 5, c5, False, 8)
+        # a disconnected one is refused
         with pytest.raises(G.GpmError) as e:
-            G.gpm_plan(h.handle, G.pattern_from_edges(5, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 0)]))
+            G.gpm_plan(h.handle, G.pattern_from_edges(4, [(0, 1), (2, 3)]))
         assert e.value.name == "GPM_E_UNSUPPORTED_PATTERN"
 
 
