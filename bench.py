@@ -150,12 +150,24 @@ def roofline_for(pattern, st, seconds, props):
                 mhz = float(json.load(f).get("sm_max_mhz", mhz))
         peak = props.multi_processor_count * 4 * 32 / 3 * mhz * 1e6 / 1e9  # Gword-op/s
         achieved = st["word_ops"] / seconds / 1e9
+        # the same work against the shared-memory ceiling: a word-op of the
+        # dominant loop (triangles inside a set) reads three operand words
+        # (the set and two rows: 12 B) from shared memory, which serves 128 B
+        # per SM per clock; other word-ops read fewer, so this is an upper
+        # estimate of the bytes moved
+        smem_peak = props.multi_processor_count * 128 * mhz * 1e6 / 1e12  # TB/s
+        smem_achieved = st["word_ops"] * 12 / seconds / 1e12
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gword-op/s",
                 "frac": achieved / peak, "traffic": None,
                 "kernel": f"k_lgs_block/k_lgs_warp ({pattern}, all launches of one gpm_count)",
                 "word_ops_per_launch": st["word_ops"], "alg_bytes_per_launch": st["alg_bytes"],
                 "peak_kind": f"derived: {props.multi_processor_count} SMs x 4 x 32 lanes / 3 "
-                             f"x {mhz:.0f} MHz"}
+                             f"x {mhz:.0f} MHz",
+                "shared_memory_view": {"achieved": smem_achieved, "peak": smem_peak,
+                                       "unit": "TB/s", "frac": smem_achieved / smem_peak,
+                                       "bytes_per_word_op": 12,
+                                       "peak_kind": f"derived: {props.multi_processor_count} SMs "
+                                                    f"x 128 B x {mhz:.0f} MHz"}}
     achieved = st["alg_bytes"] / seconds / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": None, "kernel": f"k_enum/k_clique ({pattern})",
