@@ -535,7 +535,7 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "per_pattern_s": per_pat_s, "counts": counts,
             "prep_s": prep_s, "gen_s": gen_s,
-            "gpu_launches": len(pats) * args.steps,
+            "gpu_launches": args.steps * sum(G.gpm_plan_launches(plans[p]) for p in pats),
             "clocks": clocks,
             "roofline": roofline,
             "e2e": {"value": world * g.m / e2e_s, "unit": "edges/s", "h2d_bytes_per_step": h2d,

@@ -604,6 +604,12 @@ gpm_status gpm_pattern_describe(const gpm_pattern* pattern, int induced, uint32_
   return d.size() < len ? GPM_OK : fail(GPM_E_CAPACITY, "gpm_pattern_describe: text truncated");
 }
 
+gpm_status gpm_plan_launches(const gpm_plan_t* p, uint32_t* n) {
+  if (!p || !n) return fail(GPM_E_INVALID_ARG, "gpm_plan_launches: NULL argument");
+  *n = p->launches_last;
+  return GPM_OK;
+}
+
 gpm_status gpm_plan_describe(const gpm_plan_t* p, char* buf, size_t len) {
   if (!p || !buf || len == 0) return fail(GPM_E_INVALID_ARG, "gpm_plan_describe: bad argument");
   static const char* kNames[] = {"", "k-clique", "diamond", "4-cycle", "tailed-triangle",
@@ -627,13 +633,22 @@ cudaError_t plan_launch_async(gpm_plan_t* p, uint64_t lo, uint64_t hi, uint32_t*
                               uint64_t cap, cudaStream_t s) {
   hi = std::min(hi, p->tasks.count);
   lo = std::min(lo, hi);
+  p->launches_last = 0;
   cudaError_t e = cudaMemsetAsync(p->ctl_d, 0, sizeof(Control), s);
   if (e == cudaSuccess && hi > lo) {
-    if (p->wedge && lo == 0 && hi == p->tasks.count)
+    if (p->wedge && lo == 0 && hi == p->tasks.count) {
       e = launch_cycle4_wedge(p->csr, p->graph->deg32_d, p->wedge_cnt, p->wedge_blocks, p->ctl_d,
                               p->cfg.stats ? p->ctl_d->stats : nullptr, s);
-    else
-      e = p->lgs ? launch_lgs(p, lo, hi, s) : launch_enum(p, lo, hi, list_out, cap, s);
+      p->launches_last = 1;
+    } else if (p->lgs) {
+      e = launch_lgs(p, lo, hi, s);
+      // one launch per non-empty size class, plus the arc roots and their overflow pass
+      for (int c = 0; c < 4; c++) p->launches_last += p->lgs_count[c] ? 1u : 0u;
+      if (p->heavy_count) p->launches_last += 2;
+    } else {
+      e = launch_enum(p, lo, hi, list_out, cap, s);
+      p->launches_last = 1;
+    }
   }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(p->host_pinned, p->ctl_d, sizeof(Control), cudaMemcpyDeviceToHost, s);

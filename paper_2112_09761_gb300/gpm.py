@@ -81,6 +81,7 @@ def lib():
                                ctypes.POINTER(gpm_plan_opts), vp, ctypes.POINTER(vp)]
         L.gpm_plan_info.argtypes = [vp, u64p, u32p]
         L.gpm_plan_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+        L.gpm_plan_launches.argtypes = [vp, u32p]
         L.gpm_pattern_describe.argtypes = [ctypes.POINTER(gpm_pattern), ctypes.c_int, u32, u64,
                                            ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t]
         L.gpm_count.argtypes = [vp, u64p, vp]
@@ -236,6 +237,13 @@ def gpm_plan_info(p) -> dict:
     nt, k = ctypes.c_uint64(), ctypes.c_uint32()
     _check(lib().gpm_plan_info(p, ctypes.byref(nt), ctypes.byref(k)))
     return {"n_tasks": nt.value, "k": k.value}
+
+
+def gpm_plan_launches(p) -> int:
+    """Kernels enqueued by the plan's last evaluation."""
+    n = ctypes.c_uint32()
+    _check(lib().gpm_plan_launches(p, ctypes.byref(n)))
+    return n.value
 
 
 def gpm_plan_describe(p) -> str:
