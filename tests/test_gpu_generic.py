@@ -124,3 +124,17 @@ def test_generic_task_ranges_add_up():
         cuts = sorted({0, nt, *rng.integers(0, nt, 7).tolist()})
         parts = [G.gpm_count_range(p, a, b) for a, b in zip(cuts, cuts[1:])]
         assert sum(parts) == G.gpm_count(p) == O.count_any(g, k, edges, False, 8)
+
+
+def test_generic_degenerate_graphs():
+    # no edges, fewer vertices than the pattern, trees, a graph equal to the pattern
+    cases = [gg.empty(5), gg.empty(3), gg.path(4), gg.star(6), gg.complete(5), gg.cycle(5)]
+    for g in cases:
+        with G.Graph.from_csr(g) as h:
+            for name in ("5-cycle", "house", "4-star", "5-path"):
+                k, edges = EXTRA_PATTERNS[name]
+                pat = G.pattern_from_edges(k, edges)
+                for induced in (False, True):
+                    want = O.count_any(g, k, edges, induced) if g.n >= k else 0
+                    assert h.count(pat, induced=induced) == want, (g.n, name, induced)
+                    assert h.count(pat, induced=induced, opts={"vertex_parallel": 1}) == want
