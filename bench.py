@@ -469,7 +469,10 @@ def main():
     barrier()
     clocks = sampler.stop()
     total_ms = start.elapsed_time(stop)
-    per_pat_s = {p: statistics.mean(a.elapsed_time(b) for a, b in ev[p]) / 1e3 for p in pats}
+    run_s = {p: [a.elapsed_time(b) / 1e3 for a, b in ev[p]] for p in pats}
+    per_pat_s = {p: statistics.mean(run_s[p]) for p in pats}
+    per_pat_stats = {p: {"min": min(run_s[p]), "median": statistics.median(run_s[p]),
+                         "runs": len(run_s[p])} for p in pats}
     step_s = total_ms / 1e3 / args.steps
     if dist is not None:
         t = torch.tensor([step_s], device="cuda", dtype=torch.float64)
@@ -533,7 +536,7 @@ def main():
                        "max_out_degree": graph.info()["max_out_degree"],
                        "l2": "inputs larger than L2 (CSR + DAG > 129 MB)",
                        "parallelism": f"replicas x{world}"},
-            "per_pattern_s": per_pat_s, "counts": counts,
+            "per_pattern_s": per_pat_s, "per_pattern_runs_s": per_pat_stats, "counts": counts,
             "prep_s": prep_s, "gen_s": gen_s,
             "gpu_launches": args.steps * sum(G.gpm_plan_launches(plans[p]) for p in pats),
             "clocks": clocks,
