@@ -105,6 +105,12 @@ bool isomorphic(uint32_t k, uint64_t a, uint64_t b) {
   return false;
 }
 
+const char* family_name(int family) {
+  static const char* kNames[] = {"?", "k-clique", "diamond", "4-cycle", "tailed-triangle",
+                                 "3-star", "4-path", "wedge", "generic"};
+  return (family >= 1 && family <= kGeneric) ? kNames[family] : kNames[0];
+}
+
 // Identify the plan family of a user pattern (k, edge list) up to isomorphism.
 bool identify(const gpm_pattern* p, int* family, uint32_t* k) {
   if (p->k < 2 || p->k > 8 || p->n_edges > 28) return false;
@@ -578,9 +584,7 @@ gpm_status gpm_pattern_describe(const gpm_pattern* pattern, int induced, uint32_
   uint32_t k = 0;
   std::string d;
   if (identify(pattern, &family, &k) && !generic) {
-    static const char* kNames[] = {"", "k-clique", "diamond", "4-cycle", "tailed-triangle",
-                                   "3-star", "4-path", "wedge", "generic"};
-    d = std::string("family: ") + kNames[family] + " (k = " + std::to_string(k) + ")";
+    d = std::string("family: ") + family_name(family) + " (k = " + std::to_string(k) + ")";
   } else {
     if (pattern->k < 3 || pattern->k > (uint32_t)kGenMaxK || pattern->n_edges > 28)
       return fail(GPM_E_UNSUPPORTED_PATTERN, "gpm_pattern_describe: patterns have 3 to 8 vertices");
@@ -612,9 +616,7 @@ gpm_status gpm_plan_launches(const gpm_plan_t* p, uint32_t* n) {
 
 gpm_status gpm_plan_describe(const gpm_plan_t* p, char* buf, size_t len) {
   if (!p || !buf || len == 0) return fail(GPM_E_INVALID_ARG, "gpm_plan_describe: bad argument");
-  static const char* kNames[] = {"", "k-clique", "diamond", "4-cycle", "tailed-triangle",
-                                 "3-star", "4-path", "wedge", "generic"};
-  std::string d = std::string("family: ") + kNames[p->family] + " (k = " + std::to_string(p->k) + ")";
+  std::string d = std::string("family: ") + family_name(p->family) + " (k = " + std::to_string(p->k) + ")";
   if (p->family == kGeneric) d += "; " + describe_gen(p->gen);
   else if (p->lgs) d += "; local graph search";
   const size_t nb = std::min(len - 1, d.size());
