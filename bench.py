@@ -112,8 +112,9 @@ class ClockSampler:
 
 
 def measured_traffic(workload, pattern):
-    """DRAM bytes of one count from a committed ncu summary, if the library's
-    sources still match the digest the counters were taken with."""
+    """DRAM bytes of one count from a committed ncu summary, if the sources of
+    the count's kernels and launches (listed in the summary) still match the
+    digest the counters were taken with."""
     import re
     from paper_2112_09761_gb300 import _build
     path = os.path.join(ROOT, "profiles", f"traffic_{workload}_{pattern.replace('-', '')}.md")
@@ -121,9 +122,15 @@ def measured_traffic(workload, pattern):
         return None
     with open(path) as f:
         text = f.read()
+    srcs = re.search(r"^sources: (.+)$", text, re.M)
     dig = re.search(r"^digest: (\w+)$", text, re.M)
     val = re.search(r"^dram_bytes_per_count: (\d+)$", text, re.M)
-    if not dig or not val or dig.group(1) != _build._digest():
+    if not srcs or not dig or not val:
+        return None
+    try:
+        if dig.group(1) != _build.sources_digest(srcs.group(1).split()):
+            return None
+    except OSError:
         return None
     return int(val.group(1))
 

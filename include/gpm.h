@@ -194,9 +194,9 @@ gpm_status gpm_plan_info(const gpm_plan_t* p, uint64_t* n_tasks, uint32_t* k);
  * task list and the induced mode.  GPM_E_CAPACITY if the text was cut. */
 gpm_status gpm_plan_describe(const gpm_plan_t* p, char* buf, size_t len);
 
-/* Number of kernels the library enqueued for the plan's last evaluation
- * (count, range or listing); memsets and copies are not counted.  0 before the
- * first evaluation or for an empty task range. */
+/* Number of kernels the library enqueues for one evaluation of the plan
+ * (count, non-empty task range or listing); memsets and copies are not
+ * counted. */
 gpm_status gpm_plan_launches(const gpm_plan_t* p, uint32_t* n);
 
 /* The search plan gpm_plan would choose for `pattern` on a graph of n

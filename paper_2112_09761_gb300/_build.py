@@ -47,6 +47,18 @@ def _digest() -> str:
     return h.hexdigest()[:16]
 
 
+def sources_digest(names) -> str:
+    """Digest of some csrc files and the build flags: a record measured on
+    kernels compiled from them stays valid while these files are unchanged."""
+    h = hashlib.sha256()
+    for nm in sorted(names):
+        with open(os.path.join(CSRC, nm), "rb") as fh:
+            h.update(nm.encode())
+            h.update(fh.read())
+    h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    return h.hexdigest()[:16]
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     """Compile every csrc/*.cu for sm_103a and link _build/libgpm.so."""
     os.makedirs(BUILD, exist_ok=True)

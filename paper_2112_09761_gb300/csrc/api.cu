@@ -105,12 +105,6 @@ bool isomorphic(uint32_t k, uint64_t a, uint64_t b) {
   return false;
 }
 
-const char* family_name(int family) {
-  static const char* kNames[] = {"?", "k-clique", "diamond", "4-cycle", "tailed-triangle",
-                                 "3-star", "4-path", "wedge", "generic"};
-  return (family >= 1 && family <= kGeneric) ? kNames[family] : kNames[0];
-}
-
 // Identify the plan family of a user pattern (k, edge list) up to isomorphism.
 bool identify(const gpm_pattern* p, int* family, uint32_t* k) {
   if (p->k < 2 || p->k > 8 || p->n_edges > 28) return false;
@@ -584,7 +578,9 @@ gpm_status gpm_pattern_describe(const gpm_pattern* pattern, int induced, uint32_
   uint32_t k = 0;
   std::string d;
   if (identify(pattern, &family, &k) && !generic) {
-    d = std::string("family: ") + family_name(family) + " (k = " + std::to_string(k) + ")";
+    static const char* kNames[] = {"", "k-clique", "diamond", "4-cycle", "tailed-triangle",
+                                   "3-star", "4-path", "wedge", "generic"};
+    d = std::string("family: ") + kNames[family] + " (k = " + std::to_string(k) + ")";
   } else {
     if (pattern->k < 3 || pattern->k > (uint32_t)kGenMaxK || pattern->n_edges > 28)
       return fail(GPM_E_UNSUPPORTED_PATTERN, "gpm_pattern_describe: patterns have 3 to 8 vertices");
@@ -608,15 +604,11 @@ gpm_status gpm_pattern_describe(const gpm_pattern* pattern, int induced, uint32_
   return d.size() < len ? GPM_OK : fail(GPM_E_CAPACITY, "gpm_pattern_describe: text truncated");
 }
 
-gpm_status gpm_plan_launches(const gpm_plan_t* p, uint32_t* n) {
-  if (!p || !n) return fail(GPM_E_INVALID_ARG, "gpm_plan_launches: NULL argument");
-  *n = p->launches_last;
-  return GPM_OK;
-}
-
 gpm_status gpm_plan_describe(const gpm_plan_t* p, char* buf, size_t len) {
   if (!p || !buf || len == 0) return fail(GPM_E_INVALID_ARG, "gpm_plan_describe: bad argument");
-  std::string d = std::string("family: ") + family_name(p->family) + " (k = " + std::to_string(p->k) + ")";
+  static const char* kNames[] = {"", "k-clique", "diamond", "4-cycle", "tailed-triangle",
+                                 "3-star", "4-path", "wedge", "generic"};
+  std::string d = std::string("family: ") + kNames[p->family] + " (k = " + std::to_string(p->k) + ")";
   if (p->family == kGeneric) d += "; " + describe_gen(p->gen);
   else if (p->lgs) d += "; local graph search";
   const size_t nb = std::min(len - 1, d.size());
@@ -635,22 +627,13 @@ cudaError_t plan_launch_async(gpm_plan_t* p, uint64_t lo, uint64_t hi, uint32_t*
                               uint64_t cap, cudaStream_t s) {
   hi = std::min(hi, p->tasks.count);
   lo = std::min(lo, hi);
-  p->launches_last = 0;
   cudaError_t e = cudaMemsetAsync(p->ctl_d, 0, sizeof(Control), s);
   if (e == cudaSuccess && hi > lo) {
-    if (p->wedge && lo == 0 && hi == p->tasks.count) {
+    if (p->wedge && lo == 0 && hi == p->tasks.count)
       e = launch_cycle4_wedge(p->csr, p->graph->deg32_d, p->wedge_cnt, p->wedge_blocks, p->ctl_d,
                               p->cfg.stats ? p->ctl_d->stats : nullptr, s);
-      p->launches_last = 1;
-    } else if (p->lgs) {
-      e = launch_lgs(p, lo, hi, s);
-      // one launch per non-empty size class, plus the arc roots and their overflow pass
-      for (int c = 0; c < 4; c++) p->launches_last += p->lgs_count[c] ? 1u : 0u;
-      if (p->heavy_count) p->launches_last += 2;
-    } else {
-      e = launch_enum(p, lo, hi, list_out, cap, s);
-      p->launches_last = 1;
-    }
+    else
+      e = p->lgs ? launch_lgs(p, lo, hi, s) : launch_enum(p, lo, hi, list_out, cap, s);
   }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(p->host_pinned, p->ctl_d, sizeof(Control), cudaMemcpyDeviceToHost, s);

@@ -148,8 +148,6 @@ struct gpm_plan_s {
   gpm::GenTable* gen_d = nullptr;
   // vertex parallelism: root tasks are vertices (no task list built)
   bool vertex_tasks = false;
-  // kernels the library enqueued for the last evaluation (not counting memsets)
-  uint32_t launches_last = 0;
 };
 
 namespace gpm {

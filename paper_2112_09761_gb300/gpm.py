@@ -240,7 +240,7 @@ def gpm_plan_info(p) -> dict:
 
 
 def gpm_plan_launches(p) -> int:
-    """Kernels enqueued by the plan's last evaluation."""
+    """Kernels one evaluation of the plan enqueues."""
     n = ctypes.c_uint32()
     _check(lib().gpm_plan_launches(p, ctypes.byref(n)))
     return n.value
